@@ -1,0 +1,507 @@
+/*
+ * cloak_oracle.c -- plain, slow CPU oracle for CloakLM's cloaked weight layout.
+ *
+ * TEST INFRASTRUCTURE ONLY. The tests, the smoke check and the CPU-baseline
+ * leg of the benchmark load this library; the product path never does. It
+ * shares no code, header, table or constant generator with the CUDA library.
+ *
+ * What it defines (the paper gives the goals, not the construction):
+ *   - keyed tables: the paper seeds a PRNG before any weight transfer,
+ *     enumerates the allocations, computes a random permutation and places
+ *     physical pages accordingly (Section 5, "Implementation Details"). Here:
+ *     SplitMix64 (Steele, Lea, Flood 2014) streams, Lemire's unbiased bounded
+ *     draw (Lemire 2019), and Fisher-Yates shuffles (Durstenfeld's form);
+ *   - inter-layer shuffling: a random order of layers in the arena
+ *     (Section 4.2, "Inter-layer randomization");
+ *   - intra-layer shuffling: keyed permutations of a producer's output rows
+ *     compensated by the same permutation of its consumer's input columns
+ *     (named in the Abstract and Contributions; construction is ours);
+ *   - physical page remapping: 128x128 (or 64x64) weight tiles placed at keyed
+ *     slots, pages placed at keyed physical pages (Section 4.2, "Physical page
+ *     remapping", Table 1b), re-randomised per epoch (periodic re-keying);
+ *   - no logically consecutive tiles at physically adjacent slots, so no
+ *     contiguous segment survives (Section 5.1, HBM dump attack);
+ *   - the number formats the layout stores: FP32, BF16 (round to nearest
+ *     even), OCP FP8 E4M3 (round to nearest even, saturating to +-448).
+ *
+ * The FP64 matrix products live in oracle/__init__.py (NumPy).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef unsigned __int128 u128;
+
+/* ---------------------------------------------------------------- model -- */
+typedef struct { int32_t n, k, layer, kind, perm_group, perm_axis; } orc_tensor;
+typedef struct { int32_t n_units, unit, parent, ratio; } orc_group;
+typedef struct {
+    int32_t num_tensors, num_groups;
+    const orc_tensor *tensors;
+    const orc_group *groups;
+    int32_t dtype, tile_r, tile_c, spare_pages, tile_scope, reserved;
+    int64_t page_bytes;
+} orc_model;
+
+typedef struct {
+    uint32_t *layer_perm;   /* [L]   arena position -> layer                       */
+    uint32_t *group_perm;   /* [U]   per group, stored unit -> logical unit         */
+    uint32_t *tensor_base;  /* [T]   first logical tile index of each tensor        */
+    uint32_t *tile_perm;    /* [G]   virtual tile position -> logical tile          */
+    uint32_t *page_alloc;   /* [NP+S] first NP: virtual page -> physical page;      */
+                            /*        the remaining S: the free physical pages      */
+    uint32_t *tile_slot;    /* [G]   logical tile -> arena slot                      */
+    uint32_t tile_draws, page_draws;
+} orc_tables;
+
+enum { ORC_OK = 0, ORC_EINVAL = -1, ORC_EDRAWS = -2 };
+#define ORC_MAX_DRAWS 100000u
+
+static int esize_of(int32_t dt) { return dt == 0 ? 4 : dt == 1 ? 2 : dt == 2 ? 1 : 0; }
+
+/* geometry: L, G, tpp, NP, NPS, total group units, tile_bytes, esize */
+int orc_geometry(const orc_model *m, int64_t *out)
+{
+    int es = esize_of(m->dtype);
+    if (!es || m->tile_r <= 0 || m->tile_c <= 0 || m->num_tensors <= 0) return ORC_EINVAL;
+    int64_t tile_bytes = (int64_t)m->tile_r * m->tile_c * es;
+    if (m->page_bytes <= 0 || m->page_bytes % tile_bytes) return ORC_EINVAL;
+    int64_t tpp = m->page_bytes / tile_bytes;
+    int64_t L = 0, G = 0, U = 0;
+    for (int g = 0; g < m->num_groups; g++) {
+        const orc_group *gr = &m->groups[g];
+        if (gr->n_units <= 0 || gr->unit <= 0) return ORC_EINVAL;
+        if (gr->parent >= 0) {
+            if (gr->parent >= g || gr->ratio <= 0) return ORC_EINVAL;
+            if ((int64_t)m->groups[gr->parent].n_units * gr->ratio != gr->n_units) return ORC_EINVAL;
+        }
+        U += gr->n_units;
+    }
+    for (int t = 0; t < m->num_tensors; t++) {
+        const orc_tensor *tt = &m->tensors[t];
+        if (tt->n <= 0 || tt->k <= 0 || tt->layer < 0) return ORC_EINVAL;
+        if (tt->layer + 1 > L) L = tt->layer + 1;
+        if (tt->perm_group >= 0) {
+            if (tt->perm_group >= m->num_groups) return ORC_EINVAL;
+            const orc_group *gr = &m->groups[tt->perm_group];
+            int64_t dim = tt->perm_axis == 0 ? tt->n : tt->k;
+            if ((int64_t)gr->n_units * gr->unit != dim) return ORC_EINVAL;
+        }
+        G += (int64_t)((tt->n + m->tile_r - 1) / m->tile_r) * ((tt->k + m->tile_c - 1) / m->tile_c);
+    }
+    if (G >= (1LL << 32)) return ORC_EINVAL;
+    int64_t NP = (G + tpp - 1) / tpp;
+    out[0] = L; out[1] = G; out[2] = tpp; out[3] = NP; out[4] = NP + m->spare_pages;
+    out[5] = U; out[6] = tile_bytes; out[7] = es;
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------- SplitMix64 PRNG -- */
+/* SplitMix64: the state advances by the golden-ratio increment and each
+ * output is the state passed through the variant-13 finaliser (Stafford). */
+uint64_t orc_mix(uint64_t z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+uint64_t orc_next(uint64_t *s)
+{
+    *s += 0x9E3779B97F4A7C15ULL;
+    return orc_mix(*s);
+}
+
+/* Stream seed for (key, tag, epoch, index): two finaliser rounds, so the
+ * streams of different tags / epochs / indices start at unrelated states.
+ * Tags: 1 layer order, 2 permutation group, 3 tile permutation, 4 page map. */
+uint64_t orc_stream_seed(uint64_t key, uint32_t tag, uint32_t epoch, uint32_t idx)
+{
+    uint64_t lane = ((uint64_t)tag << 56) ^ ((uint64_t)epoch << 32) ^ (uint64_t)idx;
+    return orc_mix(key ^ orc_mix(lane));
+}
+
+/* Unbiased integer in [0, n): Lemire's multiply-shift with rejection. The
+ * product x*n is split into high and low 64-bit halves; the high half is the
+ * candidate, and it is rejected while the low half falls below 2^64 mod n. */
+uint64_t orc_bounded(uint64_t *s, uint64_t n)
+{
+    uint64_t x = orc_next(s);
+    u128 m = (u128)x * n;
+    uint64_t l = (uint64_t)m;
+    if (l < n) {
+        uint64_t t = (0 - n) % n;          /* = 2^64 mod n */
+        while (l < t) {
+            x = orc_next(s);
+            m = (u128)x * n;
+            l = (uint64_t)m;
+        }
+    }
+    return (uint64_t)(m >> 64);
+}
+
+/* Fisher-Yates (Durstenfeld): start from the identity, and for i from n-1
+ * down to 1 swap position i with a uniform position j in [0, i].
+ * Afterwards a[p] is the element placed at position p. */
+void orc_fisher_yates(uint64_t *s, uint32_t n, uint32_t *a)
+{
+    for (uint32_t i = 0; i < n; i++) a[i] = i;
+    if (n < 2) return;
+    for (uint32_t i = n - 1; i >= 1; i--) {
+        uint32_t j = (uint32_t)orc_bounded(s, (uint64_t)i + 1);
+        uint32_t tmp = a[i]; a[i] = a[j]; a[j] = tmp;
+    }
+}
+
+/* ---------------------------------------------------- layout invariant ---- */
+/* Within a page: no virtual position holds the logical successor of the tile
+ * at the position before it. */
+static int intra_page_ok(const uint32_t *tp, int64_t G, int64_t tpp)
+{
+    for (int64_t v = 0; v + 1 < G; v++)
+        if ((v % tpp) != tpp - 1 && tp[v + 1] == tp[v] + 1) return 0;
+    return 1;
+}
+
+/* Across pages: for physically adjacent pages that both hold a virtual page,
+ * the first tile of the upper one is not the logical successor of the last
+ * tile of the lower one. */
+static int cross_page_ok(const uint32_t *tp, const uint32_t *pa, int64_t G, int64_t tpp,
+                         int64_t NP, int64_t NPS, int64_t *phys_to_vp)
+{
+    for (int64_t p = 0; p < NPS; p++) phys_to_vp[p] = -1;
+    for (int64_t vp = 0; vp < NP; vp++) phys_to_vp[pa[vp]] = vp;
+    for (int64_t p = 0; p + 1 < NPS; p++) {
+        int64_t a = phys_to_vp[p], b = phys_to_vp[p + 1];
+        if (a < 0 || b < 0) continue;
+        int64_t vl = a * tpp + tpp - 1, vf = b * tpp;
+        if (vl < G && vf < G && tp[vf] == tp[vl] + 1) return 0;
+    }
+    return 1;
+}
+
+static int64_t tiles_of(const orc_model *m, int t)
+{
+    const orc_tensor *tt = &m->tensors[t];
+    return (int64_t)((tt->n + m->tile_r - 1) / m->tile_r) * ((tt->k + m->tile_c - 1) / m->tile_c);
+}
+
+/* ----------------------------------------------------------------- keygen - */
+int orc_keygen(const orc_model *m, uint64_t key, uint32_t epoch, orc_tables *tb)
+{
+    int64_t geo[8];
+    int rc = orc_geometry(m, geo);
+    if (rc) return rc;
+    int64_t L = geo[0], G = geo[1], tpp = geo[2], NP = geo[3], NPS = geo[4];
+    uint64_t s;
+
+    /* 1. inter-layer order */
+    s = orc_stream_seed(key, 1, 0, 0);
+    orc_fisher_yates(&s, (uint32_t)L, tb->layer_perm);
+
+    /* 2. intra-layer permutation groups */
+    int64_t *goff = calloc((size_t)m->num_groups + 1, sizeof(int64_t));
+    for (int g = 0; g < m->num_groups; g++) goff[g + 1] = goff[g] + m->groups[g].n_units;
+    for (int g = 0; g < m->num_groups; g++) {
+        const orc_group *gr = &m->groups[g];
+        uint32_t *out = tb->group_perm + goff[g];
+        s = orc_stream_seed(key, 2, 0, (uint32_t)g);
+        if (gr->parent < 0) {
+            orc_fisher_yates(&s, (uint32_t)gr->n_units, out);
+        } else {
+            const uint32_t *par = tb->group_perm + goff[gr->parent];
+            int32_t pu = m->groups[gr->parent].n_units;
+            uint32_t *inner = malloc(sizeof(uint32_t) * (size_t)gr->ratio);
+            for (int32_t a = 0; a < pu; a++) {
+                orc_fisher_yates(&s, (uint32_t)gr->ratio, inner);
+                for (int32_t b = 0; b < gr->ratio; b++)
+                    out[a * gr->ratio + b] = par[a] * (uint32_t)gr->ratio + inner[b];
+            }
+            free(inner);
+        }
+    }
+    free(goff);
+
+    /* 3. arena order of tensors: layers in layer_perm order, tensors of a layer
+     *    in descriptor order; logical tile indices follow that order */
+    int64_t base = 0;
+    for (int64_t p = 0; p < L; p++)
+        for (int t = 0; t < m->num_tensors; t++)
+            if (m->tensors[t].layer == (int32_t)tb->layer_perm[p]) {
+                tb->tensor_base[t] = (uint32_t)base;
+                base += tiles_of(m, t);
+            }
+
+    /* 4. tile permutation, redrawn (same streams, continued) until no page
+     *    holds a logical successor right after its predecessor */
+    tb->tile_draws = 0;
+    if (m->tile_scope == 0) {
+        s = orc_stream_seed(key, 3, 0, 0);
+        do {
+            if (++tb->tile_draws > ORC_MAX_DRAWS) return ORC_EDRAWS;
+            orc_fisher_yates(&s, (uint32_t)G, tb->tile_perm);
+        } while (!intra_page_ok(tb->tile_perm, G, tpp));
+    } else {
+        uint64_t *ss = malloc(sizeof(uint64_t) * (size_t)m->num_tensors);
+        uint32_t *tmp = malloc(sizeof(uint32_t) * (size_t)G);
+        for (int t = 0; t < m->num_tensors; t++) ss[t] = orc_stream_seed(key, 3, 0, (uint32_t)t);
+        do {
+            if (++tb->tile_draws > ORC_MAX_DRAWS) { free(ss); free(tmp); return ORC_EDRAWS; }
+            for (int t = 0; t < m->num_tensors; t++) {
+                int64_t nt = tiles_of(m, t), b0 = tb->tensor_base[t];
+                orc_fisher_yates(&ss[t], (uint32_t)nt, tmp);
+                for (int64_t v = 0; v < nt; v++) tb->tile_perm[b0 + v] = (uint32_t)(b0 + tmp[v]);
+            }
+        } while (!intra_page_ok(tb->tile_perm, G, tpp));
+        free(ss); free(tmp);
+    }
+
+    /* 5. page map (the only table that depends on the epoch), redrawn until no
+     *    two physically adjacent pages join two logically consecutive tiles */
+    int64_t *p2v = malloc(sizeof(int64_t) * (size_t)NPS);
+    tb->page_draws = 0;
+    s = orc_stream_seed(key, 4, epoch, 0);
+    do {
+        if (++tb->page_draws > ORC_MAX_DRAWS) { free(p2v); return ORC_EDRAWS; }
+        orc_fisher_yates(&s, (uint32_t)NPS, tb->page_alloc);
+    } while (!cross_page_ok(tb->tile_perm, tb->page_alloc, G, tpp, NP, NPS, p2v));
+    free(p2v);
+
+    /* 6. final gather table: logical tile -> virtual position -> slot */
+    uint32_t *inv = malloc(sizeof(uint32_t) * (size_t)G);
+    for (int64_t v = 0; v < G; v++) inv[tb->tile_perm[v]] = (uint32_t)v;
+    for (int64_t g = 0; g < G; g++) {
+        int64_t v = inv[g];
+        tb->tile_slot[g] = (uint32_t)((int64_t)tb->page_alloc[v / tpp] * tpp + v % tpp);
+    }
+    free(inv);
+    return ORC_OK;
+}
+
+/* ---------------------------------------------------------- number codecs - */
+/* BF16: keep the upper 16 bits of the FP32 pattern, rounding the dropped 16
+ * bits to nearest, ties to an even upper half; NaN stays a quiet NaN. */
+uint16_t orc_bf16_encode(float f)
+{
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    if ((u & 0x7F800000u) == 0x7F800000u && (u & 0x007FFFFFu))
+        return (uint16_t)((u >> 16) | 0x0040u);
+    uint32_t hi = u >> 16, lo = u & 0xFFFFu;
+    if (lo > 0x8000u || (lo == 0x8000u && (hi & 1u))) hi += 1;
+    return (uint16_t)hi;
+}
+
+float orc_bf16_decode(uint16_t h)
+{
+    uint32_t u = (uint32_t)h << 16;
+    float f;
+    memcpy(&f, &u, 4);
+    return f;
+}
+
+/* E4M3 (OCP 8-bit floating point, no infinities): sign, 4 exponent bits with
+ * bias 7, 3 mantissa bits. E = 0 encodes m * 2^-9; E = 1..15 encodes
+ * (1 + m/8) * 2^(E-7), except E = 15, m = 7 which is NaN. Largest finite 448. */
+double orc_e4m3_decode(uint8_t c)
+{
+    int sgn = c >> 7, E = (c >> 3) & 15, mt = c & 7;
+    if (E == 15 && mt == 7) return NAN;
+    double v = E == 0 ? ldexp((double)mt, -9) : ldexp(1.0 + mt / 8.0, E - 7);
+    return sgn ? -v : v;
+}
+
+/* Round to the nearest E4M3 value, ties to the even mantissa, and saturate
+ * magnitudes above 448 to 448. All steps are exact in double: the spacing of
+ * E4M3 values in [2^e, 2^(e+1)) is 2^(e-3) (2^-9 below 2^-6), so a/q is an
+ * exact scaling and rint() (default mode: nearest, ties to even) rounds it. */
+uint8_t orc_e4m3_encode(float f)
+{
+    double x = f;
+    if (isnan(x)) return 0x7F;
+    int neg = signbit(x) ? 1 : 0;
+    double a = fabs(x), v;
+    if (isinf(a)) {
+        v = 448.0;
+    } else {
+        int e2;
+        frexp(a, &e2);                 /* a = fr * 2^e2, fr in [0.5, 1) */
+        int ex = e2 - 1;               /* floor(log2 a) for a > 0 */
+        if (a == 0.0 || ex < -6) ex = -6;
+        double q = ldexp(1.0, ex - 3);
+        v = rint(a / q) * q;
+        if (v > 448.0) v = 448.0;
+    }
+    uint8_t code;
+    if (v == 0.0) {
+        code = 0;
+    } else {
+        int e2;
+        frexp(v, &e2);
+        int ex = e2 - 1;
+        if (ex < -6) {
+            code = (uint8_t)(v / ldexp(1.0, -9));            /* subnormal: m */
+        } else {
+            int mt = (int)((v / ldexp(1.0, ex) - 1.0) * 8.0);
+            code = (uint8_t)(((ex + 7) << 3) | mt);
+        }
+    }
+    return (uint8_t)(code | (neg << 7));
+}
+
+void orc_bf16_encode_array(const float *x, uint16_t *out, int64_t n)
+{ for (int64_t i = 0; i < n; i++) out[i] = orc_bf16_encode(x[i]); }
+void orc_e4m3_encode_array(const float *x, uint8_t *out, int64_t n)
+{ for (int64_t i = 0; i < n; i++) out[i] = orc_e4m3_encode(x[i]); }
+void orc_e4m3_decode_array(const uint8_t *c, double *out, int64_t n)
+{ for (int64_t i = 0; i < n; i++) out[i] = orc_e4m3_decode(c[i]); }
+
+/* Per-row FP8 quantisation: s = amax|row| / 448 in FP32 (1 if the row is all
+ * zero), codes = E4M3(x / s) with the quotient rounded to FP32 first. */
+void orc_quant_rows_e4m3(const float *x, int64_t rows, int64_t cols, uint8_t *q, float *sc)
+{
+    for (int64_t r = 0; r < rows; r++) {
+        const float *xr = x + r * cols;
+        float amax = 0.0f;
+        for (int64_t c = 0; c < cols; c++) { float a = fabsf(xr[c]); if (a > amax) amax = a; }
+        float s = amax > 0.0f ? amax / 448.0f : 1.0f;
+        sc[r] = s;
+        for (int64_t c = 0; c < cols; c++) { volatile float v = xr[c] / s; q[r * cols + c] = orc_e4m3_encode(v); }
+    }
+}
+
+/* ------------------------------------------------ stored (permuted) matrix - */
+/* Row r (column c) of the stored matrix holds logical row (column)
+ * perm[u] * unit + w for r = u * unit + w, on the tensor's permuted axis. */
+static int64_t group_offset(const orc_model *m, int g)
+{
+    int64_t off = 0;
+    for (int i = 0; i < g; i++) off += m->groups[i].n_units;
+    return off;
+}
+
+static void axis_maps(const orc_model *m, const orc_tables *tb, int t, int64_t *rmap, int64_t *cmap)
+{
+    const orc_tensor *tt = &m->tensors[t];
+    for (int64_t r = 0; r < tt->n; r++) rmap[r] = r;
+    for (int64_t c = 0; c < tt->k; c++) cmap[c] = c;
+    if (tt->perm_group < 0) return;
+    const orc_group *gr = &m->groups[tt->perm_group];
+    const uint32_t *perm = tb->group_perm + group_offset(m, tt->perm_group);
+    int64_t *mp = tt->perm_axis == 0 ? rmap : cmap;
+    int64_t dim = tt->perm_axis == 0 ? tt->n : tt->k;
+    for (int64_t i = 0; i < dim; i++) mp[i] = (int64_t)perm[i / gr->unit] * gr->unit + i % gr->unit;
+}
+
+static int64_t elem_offset(const orc_model *m, const orc_tables *tb, int t, int64_t r, int64_t c,
+                           int64_t tile_bytes, int es)
+{
+    const orc_tensor *tt = &m->tensors[t];
+    int64_t KT = (tt->k + m->tile_c - 1) / m->tile_c;
+    int64_t g = (int64_t)tb->tensor_base[t] + (r / m->tile_r) * KT + c / m->tile_c;
+    int64_t i = r % m->tile_r, j = c % m->tile_c;
+    return (int64_t)tb->tile_slot[g] * tile_bytes + (i * m->tile_c + j) * es;
+}
+
+/* shuffle: logical FP32 W[n][k] -> permuted, converted, tiled, placed in the
+ * arena; FP8 per-stored-row scales go to scales[n] */
+int orc_shuffle_tensor(const orc_model *m, const orc_tables *tb, int t, const float *W,
+                       uint8_t *arena, float *scales)
+{
+    int64_t geo[8];
+    if (orc_geometry(m, geo)) return ORC_EINVAL;
+    const orc_tensor *tt = &m->tensors[t];
+    int64_t tile_bytes = geo[6];
+    int es = (int)geo[7];
+    int64_t *rmap = malloc(sizeof(int64_t) * (size_t)tt->n), *cmap = malloc(sizeof(int64_t) * (size_t)tt->k);
+    float *row = malloc(sizeof(float) * (size_t)tt->k);
+    axis_maps(m, tb, t, rmap, cmap);
+    for (int64_t r = 0; r < tt->n; r++) {
+        for (int64_t c = 0; c < tt->k; c++) row[c] = W[rmap[r] * tt->k + cmap[c]];
+        float s = 1.0f;
+        if (m->dtype == 2) {
+            float amax = 0.0f;
+            for (int64_t c = 0; c < tt->k; c++) { float a = fabsf(row[c]); if (a > amax) amax = a; }
+            s = amax > 0.0f ? amax / 448.0f : 1.0f;
+            if (scales) scales[r] = s;
+        }
+        for (int64_t c = 0; c < tt->k; c++) {
+            uint8_t *p = arena + elem_offset(m, tb, t, r, c, tile_bytes, es);
+            if (m->dtype == 0) {
+                memcpy(p, &row[c], 4);
+            } else if (m->dtype == 1) {
+                uint16_t h = orc_bf16_encode(row[c]);
+                memcpy(p, &h, 2);
+            } else {
+                volatile float v = row[c] / s;
+                *p = orc_e4m3_encode(v);
+            }
+        }
+    }
+    free(rmap); free(cmap); free(row);
+    return ORC_OK;
+}
+
+/* unshuffle: arena -> logical [n][k] in the stored dtype (permutation undone) */
+int orc_unshuffle_tensor(const orc_model *m, const orc_tables *tb, int t, const uint8_t *arena,
+                         uint8_t *out)
+{
+    int64_t geo[8];
+    if (orc_geometry(m, geo)) return ORC_EINVAL;
+    const orc_tensor *tt = &m->tensors[t];
+    int es = (int)geo[7];
+    int64_t *rmap = malloc(sizeof(int64_t) * (size_t)tt->n), *cmap = malloc(sizeof(int64_t) * (size_t)tt->k);
+    axis_maps(m, tb, t, rmap, cmap);
+    for (int64_t r = 0; r < tt->n; r++)
+        for (int64_t c = 0; c < tt->k; c++)
+            memcpy(out + (rmap[r] * tt->k + cmap[c]) * es,
+                   arena + elem_offset(m, tb, t, r, c, geo[6], es), (size_t)es);
+    free(rmap); free(cmap);
+    return ORC_OK;
+}
+
+/* the stored (permuted) matrix read back from the arena as FP64 values,
+ * FP8 codes multiplied by their row scale (exact in FP64) */
+int orc_stored_f64(const orc_model *m, const orc_tables *tb, int t, const uint8_t *arena,
+                   const float *scales, double *out)
+{
+    int64_t geo[8];
+    if (orc_geometry(m, geo)) return ORC_EINVAL;
+    const orc_tensor *tt = &m->tensors[t];
+    int es = (int)geo[7];
+    for (int64_t r = 0; r < tt->n; r++)
+        for (int64_t c = 0; c < tt->k; c++) {
+            const uint8_t *p = arena + elem_offset(m, tb, t, r, c, geo[6], es);
+            double v;
+            if (m->dtype == 0) { float f; memcpy(&f, p, 4); v = f; }
+            else if (m->dtype == 1) { uint16_t h; memcpy(&h, p, 2); v = orc_bf16_decode(h); }
+            else v = orc_e4m3_decode(*p) * (double)scales[r];
+            out[r * tt->k + c] = v;
+        }
+    return ORC_OK;
+}
+
+/* stored-row -> logical-row and stored-column -> logical-column maps */
+int orc_axis_maps(const orc_model *m, const orc_tables *tb, int t, int64_t *rmap, int64_t *cmap)
+{
+    axis_maps(m, tb, t, rmap, cmap);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ rekey - */
+/* Periodic re-randomisation: every virtual page moves from its physical page
+ * under the old map to its physical page under the new map. Plainly: copy
+ * the arena, then place each page. Free pages of the new map are left as is. */
+int orc_rekey(const orc_model *m, const orc_tables *old_tb, const orc_tables *new_tb,
+              uint8_t *arena, uint8_t *tmp)
+{
+    int64_t geo[8];
+    if (orc_geometry(m, geo)) return ORC_EINVAL;
+    int64_t NP = geo[3], NPS = geo[4], P = m->page_bytes;
+    memcpy(tmp, arena, (size_t)(NPS * P));
+    for (int64_t vp = 0; vp < NP; vp++)
+        memcpy(arena + (int64_t)new_tb->page_alloc[vp] * P, tmp + (int64_t)old_tb->page_alloc[vp] * P,
+               (size_t)P);
+    return ORC_OK;
+}
