@@ -1,0 +1,426 @@
+#!/usr/bin/env python3
+"""Cloaked decode throughput of a 7B-class decoder layer on one GB300.
+
+Workload: one LLaMA-7B-shaped decoder layer in BF16 (d_model 4096, 32 heads
+of 128, gated MLP 11008; Wq, Wk, Wv, Wo, Wgate, Wup, Wdown = 12,352 tiles of
+128x128, 404.75 MB), stored in the keyed, shuffled arena (2 MiB pages), random
+N(0, 0.02) weights drawn on the device, N(0, 1) activations. A step is one
+decode pass: the seven cloaked linears at batch M, replayed from a CUDA graph.
+The metric is algorithmic bytes (weights + gather table + activations in and
+out) per second. The uncloaked twin kernel (same code, arithmetic tile
+addresses) runs beside it: the cloaking overhead is the ratio.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+--impl reference times the CPU oracle (FP64 product on the logical weights,
+read back through the tables) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import os
+
+# the oracle leg is timed single-threaded (BLAS threads pinned before numpy loads)
+for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import argparse
+import hashlib
+import json
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cloaked decode GEMV GB/s (7B-class BF16 decoder layer)"
+WORKLOAD = ("7B-class decoder layer, BF16, d_model 4096, 32x128 heads, gated MLP 11008, "
+            "7 cloaked linears per decode step, 128x128 tiles over 2 MiB keyed pages")
+KEY = 0x1234
+
+
+def step_bytes(model, M):
+    """Algorithmic bytes of one decode step: every weight tile once (2 B per
+    element), its 4-byte gather-table entry, x in and y out (BF16)."""
+    b = 0
+    for t in model.tensors:
+        nt, kt = model.tiles_of(t)
+        b += t.n * t.k * 2 + 4 * nt * kt + M * (t.k + t.n) * 2
+    return b
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "100",
+                                       "-i", str(index)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.count(",") >= 8]
+        os.unlink(self.f.name)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+                power.append(float(r[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        busy = [s for s, p in zip(sm, power) if p > 0.3 * max(power)] if power else sm
+        return {"sm_mhz": statistics.median(busy) if busy else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+# ------------------------------------------------------------- distributed
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws == 1:
+        return 0, 1, 0
+    import torch
+    import torch.distributed as dist
+    rank, local = int(os.environ["RANK"]), int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    return rank, ws, local
+
+
+def max_over_ranks(v: float, ws: int) -> float:
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ------------------------------------------------------------ oracle (CPU)
+
+def oracle_sample(model, seconds=12.0, M=1):
+    """Time the CPU oracle's cloaked linear (stored matrix read back through
+    the tables in C, then the FP64 product in NumPy) over the layer's tensors
+    in turn until `seconds` of work: returns (GB/s of weights, sample text)."""
+    import oracle as O
+    from paper_2606_18400_gb300 import synth
+    om = O.OracleModel(model)
+    tb = O.keygen(om, KEY, 0)
+    Ws = synth.weights_host(model, seed=0)
+    arena, scales = O.shuffle_model(om, tb, Ws)
+    del Ws
+    xs = [synth.activations_host(M, t.k, seed=1 + i) for i, t in enumerate(model.tensors)]
+    done_b, t0, n = 0, time.perf_counter(), 0
+    while True:
+        i = n % len(model.tensors)
+        tt = model.tensors[i]
+        O.cloaked_linear(om, tb, i, arena, xs[i])
+        done_b += tt.n * tt.k * 2 + M * (tt.n + tt.k) * 2
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= seconds and n >= len(model.tensors):
+            break
+    return done_b / el / 1e9, el, n
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2606_18400_gb300 import synth
+    import oracle as O
+    O.build()
+    model = synth.llama7b_layer(1)
+    om = O.OracleModel(model)
+    tb = O.keygen(om, KEY, 0)
+    Ws = synth.weights_host(model, seed=0)
+    arena, _ = O.shuffle_model(om, tb, Ws)
+    del Ws
+    M = args.M
+    xs = [synth.activations_host(M, t.k, seed=1 + i) for i, t in enumerate(model.tensors)]
+    # a step: the oracle's cloaked linear of one tensor of the layer, in turn
+    def step(s):
+        i = s % len(model.tensors)
+        O.cloaked_linear(om, tb, i, arena, xs[i])
+        tt = model.tensors[i]
+        return tt.n * tt.k * 2 + 4 * (-(-tt.n // 128)) * (-(-tt.k // 128)) + M * (tt.n + tt.k) * 2
+    for s in range(args.warmup):
+        step(s)
+    t0 = time.perf_counter()
+    b = sum(step(args.warmup + s) for s in range(args.steps))
+    el = time.perf_counter() - t0
+    value = b / el / 1e9
+    sample = (f"{args.steps} single-tensor steps cycling over the layer's 7 tensors "
+              f"(M={M}), after {args.warmup} warm-up steps")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "batch": M},
+            "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------- GPU (cloak)
+
+def traffic_record(kernel_src):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, if it was taken on the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    rec = json.load(open(p))
+    h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+    return rec.get("dram_bytes_per_step") if rec.get("source_sha") == h else None
+
+
+def run_cloak(args):
+    import torch
+    from paper_2606_18400_gb300 import cloak, synth
+
+    rank, ws, local = dist_setup()
+    dev = local
+    torch.cuda.set_device(dev)
+    cloak.load()
+    model = synth.llama7b_layer(1)
+    T = len(model.tensors)
+    cm = cloak.CloakModel(model, device=dev, twin=True)
+    stream = torch.cuda.current_stream()
+
+    t0 = time.perf_counter()
+    cm.keygen(KEY + rank, 0)
+    keygen_ms = (time.perf_counter() - t0) * 1e3
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    shuffle_ms = 0.0
+    for t in range(T):
+        w = synth.weights_device(model, t, seed=0)
+        ev0.record()
+        cm.shuffle(t, w)
+        ev1.record()
+        torch.cuda.synchronize()
+        shuffle_ms += ev0.elapsed_time(ev1)
+        del w
+    shuffle_gbs = sum(t.n * t.k * (4 + 2 * 2) for t in model.tensors) / (shuffle_ms / 1e3) / 1e9
+
+    def make_io(M):
+        xs = [torch.from_numpy(synth.activations_host(M, t.k, seed=1 + i)).cuda().to(torch.bfloat16)
+              for i, t in enumerate(model.tensors)]
+        ys = [torch.empty((M, t.n), dtype=torch.bfloat16, device="cuda") for t in model.tensors]
+        return xs, ys
+
+    def step_fn(xs, ys, M, unc):
+        flags = cloak.LINEAR_UNCLOAKED if unc else 0
+        for t in range(T):
+            cloak.cloak_linear(cm.ctx, t, xs[t].data_ptr(), ys[t].data_ptr(), M, cloak.OUT_BF16,
+                               flags, stream.cuda_stream)
+
+    def graph_of(xs, ys, M, unc):
+        for _ in range(2):
+            step_fn(xs, ys, M, unc)  # allocate workspaces outside the capture
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        n0 = cm.launches()
+        with torch.cuda.graph(g, stream=stream):
+            step_fn(xs, ys, M, unc)
+        return g, cm.launches() - n0
+
+    def time_graph(g, K, W):
+        for _ in range(W):
+            g.replay()
+        torch.cuda.synchronize()
+        barrier(ws)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(K):
+            g.replay()
+        b.record()
+        torch.cuda.synchronize()
+        barrier(ws)
+        return max_over_ranks(a.elapsed_time(b) / K, ws)
+
+    clocks = ClockSampler(dev)
+    M = args.M
+    xs, ys = make_io(M)
+    g_cl, launches_per_step = graph_of(xs, ys, M, False)
+    g_un, _ = graph_of(xs, ys, M, True)
+    ms = time_graph(g_cl, args.steps, args.warmup)
+    ms_un = time_graph(g_un, args.steps, args.warmup)
+    B = step_bytes(model, M)
+    value = B / (ms / 1e3) / 1e9 * ws
+
+    # per-launch kernel durations for the roofline: a GPU-side sleep lets the
+    # host queue every launch and event first, so launches run back to back
+    reps = 20
+    evs = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            for _ in range(T)] for _ in range(reps)]
+    torch.cuda.synchronize()
+    torch.cuda._sleep(50_000_000)
+    for r in range(reps):
+        for t in range(T):
+            evs[r][t][0].record()
+            cloak.cloak_linear(cm.ctx, t, xs[t].data_ptr(), ys[t].data_ptr(), M, cloak.OUT_BF16, 0,
+                               stream.cuda_stream)
+            evs[r][t][1].record()
+    torch.cuda.synchronize()
+    kern_ms = sum(a.elapsed_time(b) for row in evs for a, b in row) / reps
+    per_tensor_us = [statistics.median(evs[r][t][0].elapsed_time(evs[r][t][1]) for r in range(reps)) * 1e3
+                     for t in range(T)]
+    peaks = {}
+    pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pp):
+        peaks = json.load(open(pp))
+    hbm = peaks.get("hbm_gbs")
+    peak_note = "measured" if hbm else "fallback"
+    hbm = hbm or 6800.0
+    achieved = B / (kern_ms / 1e3) / 1e9
+
+    # batch sweep (cloaked / uncloaked), same method
+    sweep = {}
+    for Ms in (1, 8, 32, 64):
+        xs2, ys2 = make_io(Ms)
+        gc, _ = graph_of(xs2, ys2, Ms, False)
+        gu, _ = graph_of(xs2, ys2, Ms, True)
+        mc = time_graph(gc, max(20, args.steps), 3)
+        mu = time_graph(gu, max(20, args.steps), 3)
+        Bs = step_bytes(model, Ms)
+        sweep[str(Ms)] = {"cloaked_gbs": round(Bs / (mc / 1e3) / 1e9, 1),
+                          "uncloaked_gbs": round(Bs / (mu / 1e3) / 1e9, 1),
+                          "cloaked_us": round(mc * 1e3, 2), "uncloaked_us": round(mu * 1e3, 2)}
+        del gc, gu, xs2, ys2
+
+    # end to end through the C ABI with host buffers (copies inside the timing)
+    xh = [x.cpu().pin_memory() for x in xs]
+    yh = [torch.empty((M, t.n), dtype=torch.bfloat16).pin_memory() for t in model.tensors]
+    def e2e_step():
+        for t in range(T):
+            cloak.cloak_linear_host(cm.ctx, t, xh[t].data_ptr(), yh[t].data_ptr(), M,
+                                    cloak.OUT_BF16, 0, stream.cuda_stream)
+    for _ in range(3):
+        e2e_step()
+    torch.cuda.synchronize()
+    barrier(ws)
+    t0 = time.perf_counter()
+    ke = max(args.steps, 20)
+    for _ in range(ke):
+        e2e_step()
+    e2e_ms = max_over_ranks((time.perf_counter() - t0) / ke * 1e3, ws)
+    h2d = sum(M * t.k * 2 for t in model.tensors)
+    d2h = sum(M * t.n * 2 for t in model.tensors)
+
+    # re-key of the placed layer (in place, all 193 pages)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    rk = []
+    for e in range(1, 4):
+        a.record()
+        cm.rekey(KEY + rank, e)
+        b.record()
+        torch.cuda.synchronize()
+        rk.append(a.elapsed_time(b))
+    rekey_ms = statistics.median(rk)
+    moved = cm.NP * model.page_bytes
+    clk = clocks.stop()
+    status = cm.device_status()
+
+    if rank == 0:
+        cpu = None
+        if args.gpus == 1 and not args.no_cpu_baseline:
+            gbs, el, n = oracle_sample(model, seconds=args.cpu_seconds, M=M)
+            cpu = {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                   "sample": f"{n} single-tensor oracle linears (M={M}) over {el:.1f} s, "
+                             f"cycling over the layer's 7 tensors"}
+        traffic = traffic_record(os.path.join(ROOT, "paper_2606_18400_gb300", "csrc", "linear.cu"))
+        line = {
+            "metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "batch": M, "weight_bytes": sum(t.n * t.k * 2 for t in model.tensors),
+                       "bytes_per_step": B, "tiles": cm.G, "pages": cm.NP, "spare_pages": model.spare_pages,
+                       "launch": "CUDA graph of 7 launches per step",
+                       "l2": "inputs larger than L2: 404.75 MB of weights per step vs 129 MB L2"},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
+                         "unit": "GB/s", "frac": round(achieved / hbm, 4),
+                         "traffic": traffic, "peak_source": peak_note,
+                         "kernel": "k_linear_tc<bf16, N=16> (swap-AB tcgen05, stream-K)",
+                         "per_tensor_us": [round(v, 2) for v in per_tensor_us]},
+            "cpu_baseline": cpu,
+            "e2e": {"value": round(B / (e2e_ms / 1e3) / 1e9 * ws, 2), "unit": "GB/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "ms_per_step": e2e_ms, "api": "cloak_linear_host x7 (pinned host buffers)"},
+            "clocks": clk,
+            "gpu_launches": launches_per_step * args.steps,
+            "uncloaked": {"value": round(B / (ms_un / 1e3) / 1e9 * ws, 1), "ms_per_step": ms_un,
+                          "overhead_pct": round((ms / ms_un - 1) * 100, 2)},
+            "sweep_batch": sweep,
+            "rekey": {"ms": round(rekey_ms, 3), "moved_bytes": moved,
+                      "gbs_rw": round(2 * moved / (rekey_ms / 1e3) / 1e9, 1)},
+            "keygen_ms": round(keygen_ms, 2), "shuffle_gbs": round(shuffle_gbs, 1),
+            "device_status": status,
+        }
+        print(json.dumps(line), flush=True)
+    cm.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["cloak", "reference"], default="cloak")
+    ap.add_argument("--M", type=int, default=1)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_cloak(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,208 @@
+/*
+ * cloak.h -- C ABI of libcloak: a cloaked linear layer for one GB300 (sm_103a).
+ *
+ * CloakLM (arxiv 2606.18400) hides where model weights sit in GPU memory: the
+ * authorised execution keeps a valid logical view of the weights while raw
+ * memory shows fragmented, shuffled state (Abstract; Section 4.2). This
+ * library keeps every weight matrix as fixed-size tiles placed in HBM in a
+ * keyed order and computes y = x W^T by gathering the tiles through a table:
+ *
+ *   inter-layer shuffling   layers take a keyed order in the arena
+ *                           (Section 4.2, "Inter-layer randomization");
+ *   intra-layer shuffling   a producer's output rows and its consumer's input
+ *                           columns are permuted by the same keyed permutation,
+ *                           so the network computes the same function (named in
+ *                           the Abstract and the Contributions);
+ *   page remapping          tiles sit at keyed slots of keyed physical pages,
+ *                           re-randomised by re-keying (Section 4.2, "Physical
+ *                           page remapping"; Table 1b; Figure 7).
+ *
+ * Tables are drawn from a caller-supplied 64-bit key before any weight is
+ * placed (Section 5, "Implementation Details"): SplitMix64 streams, Lemire's
+ * unbiased bounded draw and Fisher-Yates shuffles, redrawn until no two
+ * physically adjacent slots hold logically consecutive tiles.
+ *
+ * Conventions
+ *   - Every pointer named *_dev is CUDA device memory owned by the caller;
+ *     *_host is host memory owned by the caller (pinned memory makes the
+ *     copies asynchronous). The context owns the arena, its uncloaked twin,
+ *     the tables, the FP8 scales and its workspaces.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream). Calls enqueue work on it and return; the exceptions say so.
+ *   - Every call returns a cloak_status; no exception crosses the ABI. A CUDA
+ *     error is reported as CLOAK_E_CUDA and its message is kept for
+ *     cloak_last_error().
+ *   - A context is not thread-safe; use one context per host thread.
+ *   - Weight matrices are [n, k] (out, in), row-major; y = x W^T with x [M, k]
+ *     and y [M, n], row-major.
+ */
+#ifndef CLOAK_H
+#define CLOAK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define CLOAK_API __attribute__((visibility("default")))
+#else
+#define CLOAK_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t cloak_status;
+enum {
+    CLOAK_OK = 0,
+    CLOAK_E_INVAL = -1,        /* bad argument or descriptor                    */
+    CLOAK_E_NOMEM = -2,        /* device or host allocation failed              */
+    CLOAK_E_CUDA = -3,         /* a CUDA call failed (see cloak_last_error)     */
+    CLOAK_E_TIMEOUT = -4,      /* a bounded device wait gave up                 */
+    CLOAK_E_STATE = -5,        /* call out of order (e.g. linear before keygen) */
+    CLOAK_E_UNSUPPORTED = -6,  /* shape/dtype not supported by any kernel       */
+    CLOAK_E_DRAWS = -7         /* layout invariant not met within the draw cap  */
+};
+
+/* weight storage types (all tensors of a model share one) */
+enum { CLOAK_F32 = 0, CLOAK_BF16 = 1, CLOAK_E4M3 = 2 };
+
+/* One weight matrix. perm_group >= 0 links it to an intra-layer permutation:
+ * perm_axis 0 permutes its rows (a producer), 1 its columns (a consumer). The
+ * permuted dimension must equal the group's n_units * unit. */
+typedef struct {
+    int32_t n, k;            /* rows (out features), columns (in features)  */
+    int32_t layer;           /* layer index, 0..L-1                          */
+    int32_t kind;            /* free tag (q, k, v, o, gate, up, down, ...)   */
+    int32_t perm_group;      /* -1: not permuted                             */
+    int32_t perm_axis;       /* 0 rows, 1 columns                            */
+} cloak_tensor_desc;
+
+/* A keyed permutation of n_units blocks of `unit` rows/columns. A derived
+ * group (parent >= 0, declared after its parent) has parent.n_units * ratio
+ * units: block a*ratio+b holds parent_perm[a]*ratio + inner_a[b], so grouped
+ * query heads move with their KV head. */
+typedef struct {
+    int32_t n_units, unit, parent, ratio;
+} cloak_group_desc;
+
+enum { CLOAK_MODEL_TWIN = 1 };  /* also keep an uncloaked tile-major copy */
+
+typedef struct {
+    int32_t num_tensors, num_groups;
+    const cloak_tensor_desc *tensors;
+    const cloak_group_desc *groups;
+    int32_t dtype;           /* CLOAK_F32 / CLOAK_BF16 / CLOAK_E4M3           */
+    int32_t tile_r, tile_c;  /* tile shape in elements (128x128 for the
+                                tensor-core kernels, 64x64 for FP32)          */
+    int32_t spare_pages;     /* extra physical pages left free in the arena   */
+    int32_t tile_scope;      /* 0: one tile permutation over the model;
+                                1: one per tensor (layers still shuffled)     */
+    int32_t flags;           /* CLOAK_MODEL_TWIN                              */
+    int64_t page_bytes;      /* page size, a multiple of the tile bytes       */
+} cloak_model_desc;
+
+typedef struct cloak_ctx cloak_ctx;
+
+/* Create a context on `device`: validates the descriptor, allocates the
+ * zeroed arena of (ceil(tiles / tiles_per_page) + spare_pages) pages, the twin
+ * if requested, tables and workspaces. Synchronous. */
+CLOAK_API cloak_status cloak_create(const cloak_model_desc *desc, int32_t device, cloak_ctx **out);
+
+/* Release everything the context owns. Synchronises the device first. */
+CLOAK_API cloak_status cloak_destroy(cloak_ctx *ctx);
+
+/* Geometry: out[0..7] = layers, tiles, tiles per page, pages, pages incl.
+ * spare, permutation units, tile bytes, element bytes. */
+CLOAK_API cloak_status cloak_geometry(const cloak_ctx *ctx, int64_t out[8]);
+
+/* Draw every table for (key, epoch) on the device (Section 5: the random
+ * permutation is computed before any weight is placed): layer order, group
+ * permutations, tile permutation, page map, gather table. Blocks until done
+ * (the redraw loop reads a flag back). Any placed weights become stale:
+ * shuffle again after a keygen (use cloak_rekey to move placed weights). */
+CLOAK_API cloak_status cloak_keygen(cloak_ctx *ctx, uint64_t key, uint32_t epoch, void *stream);
+
+enum {
+    CLOAK_TAB_LAYER_PERM = 0,  /* [L]   arena position -> layer               */
+    CLOAK_TAB_GROUP_PERM = 1,  /* [U]   per group: stored unit -> logical unit */
+    CLOAK_TAB_TENSOR_BASE = 2, /* [T]   first logical tile of each tensor      */
+    CLOAK_TAB_TILE_PERM = 3,   /* [G]   virtual position -> logical tile       */
+    CLOAK_TAB_PAGE_ALLOC = 4,  /* [NP+S] virtual page -> physical page, then
+                                          the free physical pages            */
+    CLOAK_TAB_TILE_SLOT = 5    /* [G]   logical tile -> arena slot             */
+};
+/* Copy one table to host memory (count entries). Synchronous. For tests and
+ * audits; the tables are secret in deployment. */
+CLOAK_API cloak_status cloak_export_table(const cloak_ctx *ctx, int32_t which, uint32_t *host_out,
+                                size_t count);
+
+/* Place tensor `tensor` from its logical FP32 weights [n, k] (device):
+ * permute rows or columns, convert to the storage type (BF16: round to
+ * nearest even; E4M3: per-stored-row scale amax/448 then round to nearest
+ * even, saturating), cut into tiles, write each tile to its keyed slot, and to
+ * the twin if present. Ragged tile edges are written as zeros. */
+CLOAK_API cloak_status cloak_shuffle(cloak_ctx *ctx, int32_t tensor, const float *logical_dev, void *stream);
+
+/* Inverse of cloak_shuffle: read the tiles back and write the logical
+ * [n, k] matrix in the storage type (FP32 values, BF16 or E4M3 bit patterns)
+ * with the permutation undone. from_twin = 1 reads the uncloaked twin. */
+CLOAK_API cloak_status cloak_unshuffle(const cloak_ctx *ctx, int32_t tensor, void *logical_dev,
+                             int32_t from_twin, void *stream);
+
+/* Device pointer to tensor `tensor`'s FP32 scales [n] in stored-row order
+ * (E4M3 models only; owned by the context). */
+CLOAK_API cloak_status cloak_scales(const cloak_ctx *ctx, int32_t tensor, const float **dev_out);
+
+/* Device pointer to the arena and its size in bytes (for audits and tests;
+ * owned by the context). which = 0 arena, 1 twin. */
+CLOAK_API cloak_status cloak_arena(const cloak_ctx *ctx, int32_t which, void **dev_out, int64_t *bytes);
+
+enum {
+    CLOAK_LINEAR_UNCLOAKED = 1,  /* run the same kernel on the twin, tiles
+                                    addressed arithmetically (tile-major)    */
+    CLOAK_LINEAR_RELU = 2        /* y = max(y, 0)                             */
+};
+enum { CLOAK_OUT_F32 = 0, CLOAK_OUT_BF16 = 1 };
+
+/* y[M, n] = x[M, k] W^T for tensor `tensor`, reading W's tiles through the
+ * gather table. W is the stored (permuted) matrix, so a producer's output
+ * comes out permuted and its consumer takes it as is. x is FP32 for FP32
+ * models and BF16 otherwise (E4M3 models quantise x per row inside the call:
+ * scale amax/448, round to nearest even). Accumulation is FP32; with the same
+ * M, the cloaked and uncloaked kernels sum in the same order and agree bit for
+ * bit. x and y must not alias; x must be 16-byte aligned. 1 <= M <= 65536. */
+CLOAK_API cloak_status cloak_linear(cloak_ctx *ctx, int32_t tensor, const void *x_dev, void *y_dev,
+                          int32_t M, int32_t out_dtype, int32_t flags, void *stream);
+
+/* cloak_linear from host buffers: copies x in, computes, copies y out and
+ * waits for the stream (synchronous). Uses a context-owned staging buffer. */
+CLOAK_API cloak_status cloak_linear_host(cloak_ctx *ctx, int32_t tensor, const void *x_host, void *y_host,
+                               int32_t M, int32_t out_dtype, int32_t flags, void *stream);
+
+/* Re-key (periodic re-randomisation, Section 4.2 and Figure 7): draw the page
+ * map of (key, new_epoch) and move every placed page to its new physical page
+ * in place, through a small staging pool, so the arena ends bit-identical to
+ * keygen(key, new_epoch) + shuffle. The key must be the one of the last
+ * keygen. Blocks until the move plan is built, then enqueues the moves and
+ * returns. Linear calls must not run concurrently with the moves: order them
+ * on the same stream or with events. */
+CLOAK_API cloak_status cloak_rekey(cloak_ctx *ctx, uint64_t key, uint32_t new_epoch, void *stream);
+
+/* Status recorded by device code (bounded waits, bounds checks) since the
+ * last call; reading it synchronises the device and clears it. */
+CLOAK_API cloak_status cloak_device_status(cloak_ctx *ctx);
+
+/* Text of the last CUDA error recorded in this context (or ""). */
+CLOAK_API const char *cloak_last_error(const cloak_ctx *ctx);
+
+/* Number of kernels this context has launched (a running count). */
+CLOAK_API int64_t cloak_launch_count(const cloak_ctx *ctx);
+
+/* Library build identification string. */
+CLOAK_API const char *cloak_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CLOAK_H */

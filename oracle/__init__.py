@@ -85,6 +85,7 @@ def lib():
         L.orc_shuffle_tensor.argtypes = [C.POINTER(_Model), C.POINTER(_Tables), C.c_int, vp, vp, vp]
         L.orc_unshuffle_tensor.argtypes = [C.POINTER(_Model), C.POINTER(_Tables), C.c_int, vp, vp]
         L.orc_stored_f64.argtypes = [C.POINTER(_Model), C.POINTER(_Tables), C.c_int, vp, vp, vp]
+        L.orc_stored_codes.argtypes = [C.POINTER(_Model), C.POINTER(_Tables), C.c_int, vp, vp, vp]
         L.orc_axis_maps.argtypes = [C.POINTER(_Model), C.POINTER(_Tables), C.c_int, vp, vp]
         L.orc_rekey.argtypes = [C.POINTER(_Model), C.POINTER(_Tables), C.POINTER(_Tables), vp, vp]
         L.orc_bf16_encode.restype = C.c_uint16
@@ -216,6 +217,27 @@ def stored_f64(om: OracleModel, tb: Tables, t: int, arena: np.ndarray, scales=No
     return out
 
 
+def stored_codes(om: OracleModel, tb: Tables, t: int, W: np.ndarray):
+    """(codes [n, k] in the storage type, in stored order; FP8 row scales or
+    None) -- the content the arena holds for tensor t, before tiling."""
+    W = np.ascontiguousarray(W, np.float32)
+    tt = om.model.tensors[t]
+    out = np.zeros((tt.n, tt.k), _NP_DT[om.model.dtype])
+    sc = np.zeros(tt.n, np.float32)
+    ct = _ctables(om, tb)
+    assert lib().orc_stored_codes(C.byref(om.c), C.byref(ct), t, _ptr(W), _ptr(out), _ptr(sc)) == 0
+    return out, (sc if om.model.dtype == 2 else None)
+
+
+def tile_of(om: OracleModel, codes: np.ndarray, nt: int, kt: int) -> np.ndarray:
+    """Bytes of tile (nt, kt) cut from a stored matrix (zero-padded)."""
+    m = om.model
+    blk = np.zeros((m.tile_r, m.tile_c), codes.dtype)
+    part = codes[nt * m.tile_r:(nt + 1) * m.tile_r, kt * m.tile_c:(kt + 1) * m.tile_c]
+    blk[:part.shape[0], :part.shape[1]] = part
+    return blk.reshape(-1).view(np.uint8)
+
+
 def axis_maps(om: OracleModel, tb: Tables, t: int):
     """(rmap, cmap): stored row r holds logical row rmap[r]; likewise columns."""
     tt = om.model.tensors[t]
@@ -280,12 +302,15 @@ def linear_f64(x64: np.ndarray, W64: np.ndarray) -> np.ndarray:
 
 def x_operand(om: OracleModel, x: np.ndarray) -> np.ndarray:
     """The activation operand as the path consumes it, in FP64: FP32 as is,
-    BF16 rounded (nearest even), FP8 quantised per token and dequantised."""
+    BF16 rounded (nearest even), or, for FP8 weights, BF16-rounded then
+    quantised per token (scale amax/448) and dequantised."""
     if om.model.dtype == 0:
         return np.asarray(x, np.float32).astype(np.float64)
+    xb = bf16_value(bf16_bits(x))
     if om.model.dtype == 1:
-        return bf16_value(bf16_bits(x))
-    q, s = quant_rows_e4m3(x)
+        return xb
+    # FP8 models take BF16 activations and quantise them per token
+    q, s = quant_rows_e4m3(xb.astype(np.float32))
     return e4m3_value(q) * s.astype(np.float64)[:, None]
 
 

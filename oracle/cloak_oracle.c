@@ -443,6 +443,45 @@ int orc_shuffle_tensor(const orc_model *m, const orc_tables *tb, int t, const fl
     return ORC_OK;
 }
 
+/* The stored (permuted, converted) matrix [n][k] in the storage type, in
+ * stored row/column order, without placing it: tile (nt, kt) of the arena is
+ * its block [nt*tile_r.., kt*tile_c..] (zero-padded at ragged edges). */
+int orc_stored_codes(const orc_model *m, const orc_tables *tb, int t, const float *W,
+                     uint8_t *out, float *scales)
+{
+    int64_t geo[8];
+    if (orc_geometry(m, geo)) return ORC_EINVAL;
+    const orc_tensor *tt = &m->tensors[t];
+    int es = (int)geo[7];
+    int64_t *rmap = malloc(sizeof(int64_t) * (size_t)tt->n), *cmap = malloc(sizeof(int64_t) * (size_t)tt->k);
+    float *row = malloc(sizeof(float) * (size_t)tt->k);
+    axis_maps(m, tb, t, rmap, cmap);
+    for (int64_t r = 0; r < tt->n; r++) {
+        for (int64_t c = 0; c < tt->k; c++) row[c] = W[rmap[r] * tt->k + cmap[c]];
+        float s = 1.0f;
+        if (m->dtype == 2) {
+            float amax = 0.0f;
+            for (int64_t c = 0; c < tt->k; c++) { float a = fabsf(row[c]); if (a > amax) amax = a; }
+            s = amax > 0.0f ? amax / 448.0f : 1.0f;
+            if (scales) scales[r] = s;
+        }
+        for (int64_t c = 0; c < tt->k; c++) {
+            uint8_t *p = out + (r * tt->k + c) * es;
+            if (m->dtype == 0) {
+                memcpy(p, &row[c], 4);
+            } else if (m->dtype == 1) {
+                uint16_t h = orc_bf16_encode(row[c]);
+                memcpy(p, &h, 2);
+            } else {
+                volatile float v = row[c] / s;
+                *p = orc_e4m3_encode(v);
+            }
+        }
+    }
+    free(rmap); free(cmap); free(row);
+    return ORC_OK;
+}
+
 /* unshuffle: arena -> logical [n][k] in the stored dtype (permutation undone) */
 int orc_unshuffle_tensor(const orc_model *m, const orc_tables *tb, int t, const uint8_t *arena,
                          uint8_t *out)

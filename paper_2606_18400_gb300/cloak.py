@@ -1,0 +1,294 @@
+"""Python binding of libcloak (include/cloak.h): argument marshalling only.
+
+Every entry point of the C ABI is exposed under its own name and takes the
+same arguments (device pointers as ints, streams as ints). ``CloakModel`` is
+a thin convenience wrapper that accepts torch tensors; all computation runs
+in the CUDA library. If the library is missing or fails to load, every call
+raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+from . import synth
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libcloak.so")
+
+OK, E_INVAL, E_NOMEM, E_CUDA, E_TIMEOUT, E_STATE, E_UNSUPPORTED, E_DRAWS = 0, -1, -2, -3, -4, -5, -6, -7
+F32, BF16, E4M3 = 0, 1, 2
+MODEL_TWIN = 1
+TAB_LAYER_PERM, TAB_GROUP_PERM, TAB_TENSOR_BASE, TAB_TILE_PERM, TAB_PAGE_ALLOC, TAB_TILE_SLOT = range(6)
+LINEAR_UNCLOAKED, LINEAR_RELU = 1, 2
+OUT_F32, OUT_BF16 = 0, 1
+
+_STATUS = {0: "CLOAK_OK", -1: "CLOAK_E_INVAL", -2: "CLOAK_E_NOMEM", -3: "CLOAK_E_CUDA",
+           -4: "CLOAK_E_TIMEOUT", -5: "CLOAK_E_STATE", -6: "CLOAK_E_UNSUPPORTED", -7: "CLOAK_E_DRAWS"}
+
+
+class CloakError(RuntimeError):
+    def __init__(self, fn, status, msg=""):
+        super().__init__(f"{fn} -> {_STATUS.get(status, status)} {msg}".strip())
+        self.status = status
+
+
+class TensorDesc(C.Structure):
+    _fields_ = [(f, C.c_int32) for f in ("n", "k", "layer", "kind", "perm_group", "perm_axis")]
+
+
+class GroupDesc(C.Structure):
+    _fields_ = [(f, C.c_int32) for f in ("n_units", "unit", "parent", "ratio")]
+
+
+class ModelDesc(C.Structure):
+    _fields_ = [("num_tensors", C.c_int32), ("num_groups", C.c_int32),
+                ("tensors", C.POINTER(TensorDesc)), ("groups", C.POINTER(GroupDesc)),
+                ("dtype", C.c_int32), ("tile_r", C.c_int32), ("tile_c", C.c_int32),
+                ("spare_pages", C.c_int32), ("tile_scope", C.c_int32), ("flags", C.c_int32),
+                ("page_bytes", C.c_int64)]
+
+
+# (name, restype, argtypes); the list is the ABI this binding expects
+_vp, _i32, _i64, _u32, _u64 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint32, C.c_uint64
+SIGNATURES = [
+    ("cloak_create", _i32, [C.POINTER(ModelDesc), _i32, C.POINTER(_vp)]),
+    ("cloak_destroy", _i32, [_vp]),
+    ("cloak_geometry", _i32, [_vp, C.POINTER(_i64)]),
+    ("cloak_keygen", _i32, [_vp, _u64, _u32, _vp]),
+    ("cloak_export_table", _i32, [_vp, _i32, C.POINTER(_u32), C.c_size_t]),
+    ("cloak_shuffle", _i32, [_vp, _i32, _vp, _vp]),
+    ("cloak_unshuffle", _i32, [_vp, _i32, _vp, _i32, _vp]),
+    ("cloak_scales", _i32, [_vp, _i32, C.POINTER(_vp)]),
+    ("cloak_arena", _i32, [_vp, _i32, C.POINTER(_vp), C.POINTER(_i64)]),
+    ("cloak_linear", _i32, [_vp, _i32, _vp, _vp, _i32, _i32, _i32, _vp]),
+    ("cloak_linear_host", _i32, [_vp, _i32, _vp, _vp, _i32, _i32, _i32, _vp]),
+    ("cloak_rekey", _i32, [_vp, _u64, _u32, _vp]),
+    ("cloak_device_status", _i32, [_vp]),
+    ("cloak_last_error", C.c_char_p, [_vp]),
+    ("cloak_launch_count", _i64, [_vp]),
+    ("cloak_version", C.c_char_p, []),
+]
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libcloak.so (raises if it is missing: build it with
+    ``paper_2606_18400_gb300.build.build()``)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"libcloak.so not found at {path}; build it first "
+                               "(python -c 'import __graft_entry__ as g; g.build()')")
+        L = C.CDLL(path)
+        for name, res, args in SIGNATURES:
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(name, rc, ctx=None):
+    if rc != OK:
+        msg = ""
+        if ctx:
+            msg = (load().cloak_last_error(ctx) or b"").decode()
+        raise CloakError(name, rc, msg)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return int(stream) if not hasattr(stream, "cuda_stream") else stream.cuda_stream
+
+
+# ---------------------------------------------------------------- thin C names
+
+def cloak_create(desc: ModelDesc, device: int = 0):
+    ctx = C.c_void_p()
+    _check("cloak_create", load().cloak_create(C.byref(desc), device, C.byref(ctx)))
+    return ctx
+
+
+def cloak_destroy(ctx):
+    _check("cloak_destroy", load().cloak_destroy(ctx))
+
+
+def cloak_geometry(ctx):
+    out = (C.c_int64 * 8)()
+    _check("cloak_geometry", load().cloak_geometry(ctx, out), ctx)
+    return list(out)
+
+
+def cloak_keygen(ctx, key: int, epoch: int, stream=None):
+    _check("cloak_keygen", load().cloak_keygen(ctx, key & (2**64 - 1), epoch, _stream(stream)), ctx)
+
+
+def cloak_export_table(ctx, which: int, count: int):
+    import numpy as np
+    out = np.zeros(max(count, 1), np.uint32)
+    _check("cloak_export_table", load().cloak_export_table(
+        ctx, which, out.ctypes.data_as(C.POINTER(C.c_uint32)), out.size), ctx)
+    return out[:count]
+
+
+def cloak_shuffle(ctx, tensor: int, logical_dev: int, stream=None):
+    _check("cloak_shuffle", load().cloak_shuffle(ctx, tensor, logical_dev, _stream(stream)), ctx)
+
+
+def cloak_unshuffle(ctx, tensor: int, logical_dev: int, from_twin: int = 0, stream=None):
+    _check("cloak_unshuffle", load().cloak_unshuffle(ctx, tensor, logical_dev, from_twin,
+                                                     _stream(stream)), ctx)
+
+
+def cloak_scales(ctx, tensor: int) -> int:
+    p = C.c_void_p()
+    _check("cloak_scales", load().cloak_scales(ctx, tensor, C.byref(p)), ctx)
+    return p.value
+
+
+def cloak_arena(ctx, which: int = 0):
+    p, n = C.c_void_p(), C.c_int64()
+    _check("cloak_arena", load().cloak_arena(ctx, which, C.byref(p), C.byref(n)), ctx)
+    return p.value, n.value
+
+
+def cloak_linear(ctx, tensor: int, x_dev: int, y_dev: int, M: int, out_dtype: int,
+                 flags: int = 0, stream=None):
+    _check("cloak_linear", load().cloak_linear(ctx, tensor, x_dev, y_dev, M, out_dtype, flags,
+                                               _stream(stream)), ctx)
+
+
+def cloak_linear_host(ctx, tensor: int, x_host: int, y_host: int, M: int, out_dtype: int,
+                      flags: int = 0, stream=None):
+    _check("cloak_linear_host", load().cloak_linear_host(ctx, tensor, x_host, y_host, M, out_dtype,
+                                                         flags, _stream(stream)), ctx)
+
+
+def cloak_rekey(ctx, key: int, new_epoch: int, stream=None):
+    _check("cloak_rekey", load().cloak_rekey(ctx, key & (2**64 - 1), new_epoch, _stream(stream)), ctx)
+
+
+def cloak_device_status(ctx) -> int:
+    return load().cloak_device_status(ctx)
+
+
+def cloak_last_error(ctx) -> str:
+    return (load().cloak_last_error(ctx) or b"").decode()
+
+
+def cloak_launch_count(ctx) -> int:
+    return load().cloak_launch_count(ctx)
+
+
+def cloak_version() -> str:
+    return load().cloak_version().decode()
+
+
+# ------------------------------------------------------------ convenience
+
+class _DevArray:
+    """Minimal __cuda_array_interface__ exporter to view context-owned
+    device memory from torch."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
+                                         "data": (int(ptr), False), "version": 3,
+                                         "strides": None}
+
+
+def _wrap_device(ptr, shape, typestr, device):
+    import torch
+    return torch.as_tensor(_DevArray(ptr, shape, typestr), device=f"cuda:{device}")
+
+
+class CloakModel:
+    """A context for a ``synth.Model``: owns the ctypes descriptor and the
+    C context, and passes torch tensors' device pointers to the C calls."""
+
+    def __init__(self, model: "synth.Model", device: int = 0, twin: bool = False):
+        self.model = model
+        T, G = len(model.tensors), len(model.groups)
+        self._t = (TensorDesc * T)(*[TensorDesc(t.n, t.k, t.layer, t.kind, t.perm_group, t.perm_axis)
+                                     for t in model.tensors])
+        self._g = (GroupDesc * max(G, 1))(*[GroupDesc(g.n_units, g.unit, g.parent, g.ratio)
+                                            for g in model.groups])
+        self.desc = ModelDesc(T, G, self._t, self._g, model.dtype, model.tile_r, model.tile_c,
+                              model.spare_pages, model.tile_scope, MODEL_TWIN if twin else 0,
+                              model.page_bytes)
+        self.device = device
+        self.ctx = cloak_create(self.desc, device)
+        (self.L, self.G, self.tpp, self.NP, self.NPS, self.U, self.tile_bytes,
+         self.esize) = cloak_geometry(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            cloak_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def keygen(self, key, epoch=0, stream=None):
+        cloak_keygen(self.ctx, key, epoch, stream)
+
+    def table(self, which):
+        n = {TAB_LAYER_PERM: self.L, TAB_GROUP_PERM: self.U,
+             TAB_TENSOR_BASE: len(self.model.tensors), TAB_TILE_PERM: self.G,
+             TAB_PAGE_ALLOC: self.NPS, TAB_TILE_SLOT: self.G}[which]
+        return cloak_export_table(self.ctx, which, n)
+
+    def shuffle(self, t, w_f32, stream=None):
+        import torch
+        assert w_f32.dtype == torch.float32 and w_f32.is_cuda and w_f32.is_contiguous()
+        tt = self.model.tensors[t]
+        assert tuple(w_f32.shape) == (tt.n, tt.k)
+        cloak_shuffle(self.ctx, t, w_f32.data_ptr(), stream)
+
+    def unshuffle(self, t, from_twin=False, stream=None):
+        import torch
+        tt = self.model.tensors[t]
+        dt = {F32: torch.float32, BF16: torch.int16, E4M3: torch.uint8}[self.model.dtype]
+        out = torch.empty((tt.n, tt.k), dtype=dt, device=f"cuda:{self.device}")
+        cloak_unshuffle(self.ctx, t, out.data_ptr(), int(from_twin), stream)
+        return out
+
+    def scales(self, t):
+        """FP32 per-stored-row scales of tensor t (a device copy)."""
+        import torch
+        torch.cuda.synchronize(self.device)
+        return _wrap_device(cloak_scales(self.ctx, t), (self.model.tensors[t].n,), "<f4",
+                            self.device).clone()
+
+    def linear(self, t, x, y=None, out_dtype=OUT_BF16, uncloaked=False, relu=False, stream=None):
+        import torch
+        tt = self.model.tensors[t]
+        M = x.shape[0]
+        if y is None:
+            y = torch.empty((M, tt.n), device=x.device,
+                            dtype=torch.float32 if out_dtype == OUT_F32 else torch.bfloat16)
+        flags = (LINEAR_UNCLOAKED if uncloaked else 0) | (LINEAR_RELU if relu else 0)
+        cloak_linear(self.ctx, t, x.data_ptr(), y.data_ptr(), M, out_dtype, flags, stream)
+        return y
+
+    def rekey(self, key, new_epoch, stream=None):
+        cloak_rekey(self.ctx, key, new_epoch, stream)
+
+    def arena_bytes(self, which=0):
+        """The arena (0) or the twin (1) as a uint8 device view (no copy)."""
+        import torch
+        ptr, n = cloak_arena(self.ctx, which)
+        torch.cuda.synchronize(self.device)
+        return _wrap_device(ptr, (n,), "|u1", self.device)
+
+    def device_status(self):
+        return cloak_device_status(self.ctx)
+
+    def launches(self):
+        return cloak_launch_count(self.ctx)

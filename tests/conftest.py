@@ -18,3 +18,13 @@ def oracle_mod():
     import oracle
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def cloak_lib():
+    """The CUDA library (built in-tree if stale). GPU tests fail loudly when
+    it cannot be built or loaded."""
+    from paper_2606_18400_gb300 import build, cloak
+    build.build()
+    cloak.load()
+    return cloak

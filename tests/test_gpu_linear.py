@@ -1,0 +1,152 @@
+"""GPU cloaked linear against the FP64 oracle (normwise relative error:
+1e-5 FP32, 1e-2 BF16, 5e-2 E4M3) and bit-exact against the uncloaked
+kernel with the same reduction order."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2606_18400_gb300 import synth
+from helpers import place_both, x_device, torch_bf16_bits
+
+pytestmark = pytest.mark.gpu
+
+TOL = {synth.DT_F32: 1e-5, synth.DT_BF16: 1e-2, synth.DT_E4M3: 5e-2}
+
+
+def run_linear(cloak, cm, t, x, out_f32=True, uncloaked=False, relu=False):
+    y = cm.linear(t, x, out_dtype=cloak.OUT_F32 if out_f32 else cloak.OUT_BF16,
+                  uncloaked=uncloaked, relu=relu)
+    torch.cuda.synchronize()
+    return y
+
+
+def check_tensor(cloak, cm, om, tb, arena, scales, t, M, seed):
+    m = om.model
+    tt = m.tensors[t]
+    x = synth.activations_host(M, tt.k, seed=seed)
+    xd = x_device(m, x)
+    if m.dtype != synth.DT_F32:
+        assert np.array_equal(torch_bf16_bits(xd), O.bf16_bits(x))  # same operand both sides
+    ref = O.cloaked_linear(om, tb, t, arena, x, scales[t] if scales else None)
+    y = run_linear(cloak, cm, t, xd).cpu().numpy()
+    err = O.relative_error(y, ref)
+    assert err <= TOL[m.dtype], (t, M, err)
+    if cm.model is not None and getattr(cm, "_twin", True):
+        yu = run_linear(cloak, cm, t, xd, uncloaked=True).cpu().numpy()
+        assert np.array_equal(y.view(np.uint32), yu.view(np.uint32)), (t, M)
+    yb = run_linear(cloak, cm, t, xd, out_f32=False)
+    yb = yb.view(torch.int16).cpu().numpy().view(np.uint16)
+    assert np.array_equal(yb, O.bf16_bits(y)), "BF16 output is the rounded FP32 result"
+    return err
+
+
+@pytest.mark.parametrize("M", [1, 3, 8, 17, 32, 64, 100, 256, 300])
+def test_small_bf16_decoder_all_tensors(cloak_lib, M):
+    m = synth.small_decoder(2, synth.DT_BF16, d_model=384, n_heads=6, n_kv_heads=2, d_ff=200,
+                            spare_pages=5)
+    cm, om, tb, arena, scales, Ws = place_both(cloak_lib, m, key=0x1234)
+    for t in range(len(m.tensors)):
+        check_tensor(cloak_lib, cm, om, tb, arena, scales, t, M, seed=M * 31 + t)
+    cm.close()
+
+
+@pytest.mark.parametrize("M", [1, 4, 16, 64, 200])
+def test_small_fp8_decoder_all_tensors(cloak_lib, M):
+    m = synth.small_decoder(2, synth.DT_E4M3, page_bytes=2 * 128 * 128, d_model=384, n_heads=6,
+                            n_kv_heads=2, d_ff=256)
+    cm, om, tb, arena, scales, Ws = place_both(cloak_lib, m, key=5)
+    for t in range(len(m.tensors)):
+        check_tensor(cloak_lib, cm, om, tb, arena, scales, t, M, seed=M * 7 + t)
+    cm.close()
+
+
+def test_fp8_quantised_operands_are_near_exact(cloak_lib):
+    """With the oracle's quantised activations the only difference left is
+    FP32 accumulation order: far below the 5e-2 bound."""
+    m = synth.small_decoder(1, synth.DT_E4M3, page_bytes=2 * 128 * 128, d_model=512, d_ff=512,
+                            n_heads=4, n_kv_heads=4, head_dim=128)
+    cm, om, tb, arena, scales, Ws = place_both(cloak_lib, m, key=9)
+    for t in range(len(m.tensors)):
+        err = check_tensor(cloak_lib, cm, om, tb, arena, scales, t, 16, seed=t)
+        assert err < 1e-5
+    cm.close()
+
+
+def test_mlp2_fp32_matches_fp64_oracle(cloak_lib):
+    """Two-layer FP32 MLP (d 256, d_ff 1024, batch 4, key 0x1234): the
+    cloaked W1 (rows permuted) and W2 (columns compensated) compute the plain
+    MLP within 1e-5 normwise; the shuffle round trip is bit-exact."""
+    m = synth.mlp2()
+    cm, om, tb, arena, scales, Ws = place_both(cloak_lib, m, key=0x1234)
+    x = synth.activations_host(4, 256, seed=1)
+    xd = x_device(m, x)
+    h = cm.linear(0, xd, out_dtype=cloak_lib.OUT_F32, relu=True)
+    y = cm.linear(1, h, out_dtype=cloak_lib.OUT_F32)
+    torch.cuda.synchronize()
+    ref = O.mlp2_f64(x.astype(np.float64), Ws[0], Ws[1])
+    assert O.relative_error(y.cpu().numpy(), ref) <= 1e-5
+    for t in range(2):
+        assert np.array_equal(cm.unshuffle(t).cpu().numpy(), Ws[t])
+    # the hidden activations are permuted exactly as the oracle permutes W1's rows
+    rmap, _ = O.axis_maps(om, tb, 0)
+    hp = np.maximum(x.astype(np.float64) @ Ws[0].astype(np.float64).T, 0)[:, rmap]
+    assert O.relative_error(h.cpu().numpy(), hp) <= 1e-5
+    cm.close()
+
+
+@pytest.mark.parametrize("M", [1, 8, 32, 64])
+def test_llama7b_layer_decode(cloak_lib, M):
+    """One 7B-class BF16 layer (Wq, Wk, Wv, Wo, Wgate, Wup, Wdown) at decode
+    batch M: each cloaked linear within 1e-2 of the FP64 oracle and
+    bit-identical to the uncloaked kernel."""
+    m = synth.llama7b_layer(1)
+    cm, om, tb, arena, scales, Ws = place_both(cloak_lib, m, key=0x1234)
+    for t in range(len(m.tensors)):
+        check_tensor(cloak_lib, cm, om, tb, arena, scales, t, M, seed=100 + t)
+    cm.close()
+
+
+def test_integer_mlp_cloaked_equals_plain_exactly(cloak_lib):
+    """Integer-valued weights and inputs keep every FP32 sum exact, so the
+    cloaked, permuted and compensated MLP equals the plain one bit for bit,
+    for several keys."""
+    m = synth.mlp2()
+    Ws = synth.int_weights_host(m, seed=3, lo=-1, hi=1)
+    x = np.random.default_rng(4).integers(-2, 3, size=(4, 256)).astype(np.float32)
+    ref = O.mlp2_f64(x.astype(np.float64), Ws[0], Ws[1])
+    for key in (1, 2, 0x1234):
+        cm, om, tb, arena, scales, _ = place_both(cloak_lib, m, key=key, weights=Ws)
+        h = cm.linear(0, torch.from_numpy(x).cuda(), out_dtype=cloak_lib.OUT_F32, relu=True)
+        y = cm.linear(1, h, out_dtype=cloak_lib.OUT_F32)
+        torch.cuda.synchronize()
+        assert np.array_equal(y.cpu().numpy().astype(np.float64), ref)
+        cm.close()
+
+
+def test_linear_host_entry_point(cloak_lib):
+    m = synth.small_decoder(1, synth.DT_BF16)
+    cm, om, tb, arena, scales, Ws = place_both(cloak_lib, m, key=3)
+    x = synth.activations_host(5, m.tensors[0].k, seed=2)
+    xb = torch.from_numpy(x).to(torch.bfloat16).pin_memory()
+    yh = torch.empty((5, m.tensors[0].n), dtype=torch.float32).pin_memory()
+    cloak_lib.cloak_linear_host(cm.ctx, 0, xb.data_ptr(), yh.data_ptr(), 5, cloak_lib.OUT_F32)
+    yd = cm.linear(0, xb.cuda(), out_dtype=cloak_lib.OUT_F32).cpu()
+    assert torch.equal(yh, yd)
+    cm.close()
+
+
+def test_bad_calls_return_errors(cloak_lib):
+    m = synth.small_decoder(1, synth.DT_BF16)
+    cm = cloak_lib.CloakModel(m)
+    x = torch.zeros((2, m.tensors[0].k), dtype=torch.bfloat16, device="cuda")
+    with pytest.raises(cloak_lib.CloakError) as e:
+        cm.linear(0, x)  # before keygen
+    assert e.value.status == cloak_lib.E_STATE
+    cm.keygen(1, 0)
+    with pytest.raises(cloak_lib.CloakError):
+        cm.linear(0, x, uncloaked=True)  # no twin
+    with pytest.raises(cloak_lib.CloakError):
+        cloak_lib.cloak_linear(cm.ctx, 99, x.data_ptr(), x.data_ptr(), 2, 0)
+    assert cm.device_status() == 0
+    cm.close()

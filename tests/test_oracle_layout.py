@@ -331,3 +331,21 @@ def test_compensated_gqa_layer_is_the_same_function():
         got = layer(S)
         assert np.max(np.abs(got - layer([w.astype(np.float32).astype(np.float64) for w in Ws]))) < 1e-12
         assert np.max(np.abs(got - ref)) < 1e-4  # FP32 storage of the weights only
+
+
+@pytest.mark.parametrize("mi", range(4))
+def test_stored_codes_are_the_placed_tiles(mi):
+    m = models()[mi]
+    om = O.OracleModel(m)
+    tb = O.keygen(om, 21, 1)
+    Ws = synth.weights_host(m, seed=3)
+    arena, scales = O.shuffle_model(om, tb, Ws)
+    for t, W in enumerate(Ws):
+        codes, sc = O.stored_codes(om, tb, t, W)
+        nt, kt = m.tiles_of(m.tensors[t])
+        for u in range(nt * kt):
+            s = int(tb.tile_slot[tb.tensor_base[t] + u])
+            assert np.array_equal(arena[s * om.tile_bytes:(s + 1) * om.tile_bytes],
+                                  O.tile_of(om, codes, u // kt, u % kt))
+        if sc is not None:
+            assert np.array_equal(sc, scales[t])
