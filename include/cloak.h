@@ -175,6 +175,16 @@ enum { CLOAK_OUT_F32 = 0, CLOAK_OUT_BF16 = 1 };
 CLOAK_API cloak_status cloak_linear(cloak_ctx *ctx, int32_t tensor, const void *x_dev, void *y_dev,
                           int32_t M, int32_t out_dtype, int32_t flags, void *stream);
 
+/* Up to 8 independent cloaked linears in one launch (e.g. the seven
+ * projections of a decoder layer): y_i = x_i W_{t_i}^T for i < n, all with M
+ * rows. Their tiles are concatenated and split evenly over the SMs, so the
+ * launch and pipeline fill are paid once. The summation order depends on the
+ * whole batch; cloaked and uncloaked batches agree bit for bit. Same rules as
+ * cloak_linear for each x_i / y_i. */
+CLOAK_API cloak_status cloak_linear_batch(cloak_ctx *ctx, int32_t n, const int32_t *tensors,
+                                          const void *const *x_dev, void *const *y_dev, int32_t M,
+                                          int32_t out_dtype, int32_t flags, void *stream);
+
 /* cloak_linear from host buffers: copies x in, computes, copies y out and
  * waits for the stream (synchronous). Uses a context-owned staging buffer. */
 CLOAK_API cloak_status cloak_linear_host(cloak_ctx *ctx, int32_t tensor, const void *x_host, void *y_host,

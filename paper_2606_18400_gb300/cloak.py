@@ -62,6 +62,8 @@ SIGNATURES = [
     ("cloak_scales", _i32, [_vp, _i32, C.POINTER(_vp)]),
     ("cloak_arena", _i32, [_vp, _i32, C.POINTER(_vp), C.POINTER(_i64)]),
     ("cloak_linear", _i32, [_vp, _i32, _vp, _vp, _i32, _i32, _i32, _vp]),
+    ("cloak_linear_batch", _i32, [_vp, _i32, C.POINTER(_i32), C.POINTER(_vp), C.POINTER(_vp), _i32,
+                                  _i32, _i32, _vp]),
     ("cloak_linear_host", _i32, [_vp, _i32, _vp, _vp, _i32, _i32, _i32, _vp]),
     ("cloak_rekey", _i32, [_vp, _u64, _u32, _vp]),
     ("cloak_device_status", _i32, [_vp]),
@@ -160,6 +162,16 @@ def cloak_linear(ctx, tensor: int, x_dev: int, y_dev: int, M: int, out_dtype: in
                  flags: int = 0, stream=None):
     _check("cloak_linear", load().cloak_linear(ctx, tensor, x_dev, y_dev, M, out_dtype, flags,
                                                _stream(stream)), ctx)
+
+
+def cloak_linear_batch(ctx, tensors, x_devs, y_devs, M: int, out_dtype: int, flags: int = 0,
+                       stream=None):
+    n = len(tensors)
+    ta = (C.c_int32 * n)(*tensors)
+    xa = (C.c_void_p * n)(*x_devs)
+    ya = (C.c_void_p * n)(*y_devs)
+    _check("cloak_linear_batch", load().cloak_linear_batch(ctx, n, ta, xa, ya, M, out_dtype, flags,
+                                                           _stream(stream)), ctx)
 
 
 def cloak_linear_host(ctx, tensor: int, x_host: int, y_host: int, M: int, out_dtype: int,
@@ -276,6 +288,19 @@ class CloakModel:
         flags = (LINEAR_UNCLOAKED if uncloaked else 0) | (LINEAR_RELU if relu else 0)
         cloak_linear(self.ctx, t, x.data_ptr(), y.data_ptr(), M, out_dtype, flags, stream)
         return y
+
+    def linear_batch(self, tensors, xs, ys=None, out_dtype=OUT_BF16, uncloaked=False, relu=False,
+                     stream=None):
+        import torch
+        M = xs[0].shape[0]
+        if ys is None:
+            ys = [torch.empty((M, self.model.tensors[t].n), device=xs[0].device,
+                              dtype=torch.float32 if out_dtype == OUT_F32 else torch.bfloat16)
+                  for t in tensors]
+        flags = (LINEAR_UNCLOAKED if uncloaked else 0) | (LINEAR_RELU if relu else 0)
+        cloak_linear_batch(self.ctx, list(tensors), [x.data_ptr() for x in xs],
+                           [y.data_ptr() for y in ys], M, out_dtype, flags, stream)
+        return ys
 
     def rekey(self, key, new_epoch, stream=None):
         cloak_rekey(self.ctx, key, new_epoch, stream)

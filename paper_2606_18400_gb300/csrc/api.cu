@@ -328,6 +328,24 @@ extern "C" cloak_status cloak_linear(cloak_ctx *ctx, int32_t tensor, const void 
     return linear_run(ctx, tensor, x_dev, y_dev, M, out_dtype, flags, (cudaStream_t)stream);
 }
 
+extern "C" cloak_status cloak_linear_batch(cloak_ctx *ctx, int32_t n, const int32_t *tensors,
+                                           const void *const *x_dev, void *const *y_dev, int32_t M,
+                                           int32_t out_dtype, int32_t flags, void *stream) {
+    if (!ctx || n < 1 || n > 8 || !tensors || !x_dev || !y_dev || M < 1 || M > 65536 ||
+        (out_dtype != CLOAK_OUT_F32 && out_dtype != CLOAK_OUT_BF16) || (flags & ~3))
+        return CLOAK_E_INVAL;
+    for (int i = 0; i < n; ++i) {
+        if (tensors[i] < 0 || tensors[i] >= (int32_t)ctx->tensors.size() || !x_dev[i] || !y_dev[i] ||
+            ((uintptr_t)x_dev[i] & 15))
+            return CLOAK_E_INVAL;
+        for (int j = 0; j < i; ++j)
+            if (tensors[j] == tensors[i]) return CLOAK_E_INVAL;  // row counters are per tensor
+    }
+    if (!ctx->keyed) return CLOAK_E_STATE;
+    if ((flags & CLOAK_LINEAR_UNCLOAKED) && !ctx->twin) return CLOAK_E_STATE;
+    return linear_batch_run(ctx, n, tensors, x_dev, y_dev, M, out_dtype, flags, (cudaStream_t)stream);
+}
+
 extern "C" cloak_status cloak_linear_host(cloak_ctx *ctx, int32_t tensor, const void *x_host,
                                           void *y_host, int32_t M, int32_t out_dtype,
                                           int32_t flags, void *stream) {

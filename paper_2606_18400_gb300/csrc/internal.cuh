@@ -132,5 +132,7 @@ cloak_status rekey_run(cloak_ctx *ctx, uint64_t key, uint32_t new_epoch, cudaStr
 // linear.cu
 cloak_status linear_run(cloak_ctx *ctx, int t, const void *x, void *y, int M, int out_dtype,
                         int flags, cudaStream_t s);
+cloak_status linear_batch_run(cloak_ctx *ctx, int n, const int32_t *tensors, const void *const *xs,
+                              void *const *ys, int M, int out_dtype, int flags, cudaStream_t s);
 
 }  // namespace cloak

@@ -126,16 +126,31 @@ __global__ void k_quant_rows(const __nv_bfloat16 *x, int K, uint8_t *q, float *s
 
 // ------------------------------------------------------ tensor-core path
 
-struct TcArgs {
-    const uint32_t *slot_of;  // gather table, nullptr: uncloaked (slot = tile index)
-    uint32_t base;            // first logical tile of the tensor
-    int N, K, NT, KT, M;
+// One launch computes up to MAXP independent linears ("problems"); their
+// tiles are concatenated, (problem, tile row, tile column)-major, and split
+// evenly over the CTAs. A decoder layer's seven linears fit one launch.
+constexpr int MAXP = 8;
+
+struct TcProblem {
+    uint64_t u_begin;                // first unit (tile) of the problem in the launch
+    uint32_t base;                   // first logical tile of the tensor
+    int N, K, NT, KT;
     void *y;
-    int out_f32, relu;
     const float *w_scale, *x_scale;  // E4M3 only
-    float *part;                     // [grid][2][128][NPAD] partial sums
     uint32_t *rowcnt;                // per tile row arrival counters (zeroed)
+};
+
+struct TcBatch {
+    const uint32_t *slot_of;  // gather table; nullptr: uncloaked (slot = tile index)
+    int np, M, out_f32, relu;
+    uint64_t total;           // units of all problems
+    float *part;              // [grid][2][128][NPAD] partial sums
     int *status;
+    TcProblem p[MAXP];
+};
+
+struct TxMaps {
+    CUtensorMap m[MAXP];      // activations of each problem, [M, K] row-major
 };
 
 template <bool FP8, int NPAD>
@@ -155,10 +170,38 @@ __device__ __forceinline__ uint32_t cta_of_unit(uint64_t u, uint64_t G, uint64_t
     return (uint32_t)(((u + 1) * G - 1) / T);
 }
 
+// position of a unit: problem, tile row, tile column, first unit of its row
+struct Loc {
+    int p;
+    uint32_t nt, kt;
+    uint64_t row_begin;
+};
+
+__device__ __forceinline__ Loc locate(const TcBatch &b, uint64_t u) {
+    int p = 0;
+    while (p + 1 < b.np && u >= b.p[p + 1].u_begin) ++p;
+    const uint64_t local = u - b.p[p].u_begin;
+    Loc l;
+    l.p = p;
+    l.nt = (uint32_t)(local / (uint32_t)b.p[p].KT);
+    l.kt = (uint32_t)(local % (uint32_t)b.p[p].KT);
+    l.row_begin = b.p[p].u_begin + (uint64_t)l.nt * b.p[p].KT;
+    return l;
+}
+
+template <bool FP8>
+__device__ __forceinline__ void store_out(const TcBatch &b, const TcProblem &P, int row, int m,
+                                          float v) {
+    if (FP8) v = v * P.w_scale[row] * P.x_scale[m];
+    if (b.relu) v = fmaxf(v, 0.0f);
+    if (b.out_f32) reinterpret_cast<float *>(P.y)[(int64_t)m * P.N + row] = v;
+    else reinterpret_cast<__nv_bfloat16 *>(P.y)[(int64_t)m * P.N + row] = __float2bfloat16_rn(v);
+}
+
 template <bool FP8, int NPAD>
 __global__ void __launch_bounds__(192, 1)
-    k_linear_tc(const __grid_constant__ CUtensorMap tw, const __grid_constant__ CUtensorMap tx,
-                TcArgs a) {
+    k_linear_tc(const __grid_constant__ CUtensorMap tw, const __grid_constant__ TxMaps tx,
+                const __grid_constant__ TcBatch b) {
     using C = TcCfg<FP8, NPAD>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>(
@@ -171,7 +214,7 @@ __global__ void __launch_bounds__(192, 1)
     volatile uint32_t *last_flag = tmem_slot + 1;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint64_t T = (uint64_t)a.NT * a.KT, G = gridDim.x;
+    const uint64_t T = b.total, G = gridDim.x;
     const uint64_t u0 = blockIdx.x * T / G, u1 = (blockIdx.x + 1) * T / G;
 
     if (threadIdx.x == 0) {
@@ -179,13 +222,13 @@ __global__ void __launch_bounds__(192, 1)
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        for (int b = 0; b < 2; ++b) {
-            mbar_init(&tfull[b], 1);
-            mbar_init(&tempty[b], 128);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&tfull[i], 1);
+            mbar_init(&tempty[i], 128);
         }
         fence_mbar_init();
         prefetch_tmap(&tw);
-        prefetch_tmap(&tx);
+        for (int p = 0; p < b.np; ++p) prefetch_tmap(&tx.m[p]);
     }
     if (warp == 1) {
         tmem_alloc(tmem_slot, C::TMEM_COLS);
@@ -199,25 +242,36 @@ __global__ void __launch_bounds__(192, 1)
     if (warp == 0) {
         if (lane == 0) {
             const uint64_t pol_w = policy_evict_first(), pol_x = policy_evict_last();
+            Loc l = locate(b, u0);
             uint32_t it = 0;
             for (uint64_t u = u0; u < u1; ++u, ++it) {
                 const int s = it % C::STAGES;
                 const uint32_t ph = (it / C::STAGES) & 1;
-                if (it >= (uint32_t)C::STAGES && !mbar_wait(&empty[s], ph ^ 1, a.status)) break;
+                if (it >= (uint32_t)C::STAGES && !mbar_wait(&empty[s], ph ^ 1, b.status)) break;
+                const TcProblem &P = b.p[l.p];
                 mbar_expect_tx(&full[s], C::STAGE);
-                const uint32_t g = a.base + (uint32_t)u;
-                const uint32_t slot = a.slot_of ? __ldg(a.slot_of + g) : g;
+                const uint32_t g = P.base + (uint32_t)(u - P.u_begin);
+                const uint32_t slot = b.slot_of ? __ldg(b.slot_of + g) : g;
                 const int32_t row = (int32_t)(slot * 128u);
-                const int32_t kc = (int32_t)(u % a.KT) * 128;
+                const int32_t kc = (int32_t)l.kt * 128;
                 uint8_t *sa = smem + s * C::STAGE, *sb = sa + C::A_BYTES;
+                const CUtensorMap *xm = &tx.m[l.p];
                 if (FP8) {
                     tma_load_2d_hint(sa, &tw, &full[s], 0, row, pol_w);
-                    tma_load_2d_hint(sb, &tx, &full[s], kc, 0, pol_x);
+                    tma_load_2d_hint(sb, xm, &full[s], kc, 0, pol_x);
                 } else {
                     tma_load_2d_hint(sa, &tw, &full[s], 0, row, pol_w);
                     tma_load_2d_hint(sa + 16384, &tw, &full[s], 64, row, pol_w);
-                    tma_load_2d_hint(sb, &tx, &full[s], kc, 0, pol_x);
-                    tma_load_2d_hint(sb + C::B_BYTES / 2, &tx, &full[s], kc + 64, 0, pol_x);
+                    tma_load_2d_hint(sb, xm, &full[s], kc, 0, pol_x);
+                    tma_load_2d_hint(sb + C::B_BYTES / 2, xm, &full[s], kc + 64, 0, pol_x);
+                }
+                // advance (problem, row, column)
+                if (++l.kt == (uint32_t)P.KT) {
+                    l.kt = 0;
+                    if (++l.nt == (uint32_t)P.NT) {
+                        l.nt = 0;
+                        ++l.p;
+                    }
                 }
             }
         }
@@ -226,15 +280,15 @@ __global__ void __launch_bounds__(192, 1)
             uint32_t it = 0, seg = 0;
             bool ok = true;
             for (uint64_t u = u0; u < u1 && ok; ++seg) {
-                const uint64_t nt = u / a.KT;
-                const uint64_t send = umin64(u1, (nt + 1) * a.KT);
-                const uint32_t b = seg & 1, use = seg >> 1;
-                if (seg >= 2 && !mbar_wait(&tempty[b], (use - 1) & 1, a.status)) break;
+                const Loc l = locate(b, u);
+                const uint64_t send = umin64(u1, l.row_begin + b.p[l.p].KT);
+                const uint32_t bf = seg & 1, use = seg >> 1;
+                if (seg >= 2 && !mbar_wait(&tempty[bf], (use - 1) & 1, b.status)) break;
                 tc_fence_after();
-                const uint32_t d = tmem + b * NPAD;
+                const uint32_t d = tmem + bf * NPAD;
                 for (uint64_t uu = u; uu < send; ++uu, ++it) {
                     const int s = it % C::STAGES;
-                    if (!mbar_wait(&full[s], (it / C::STAGES) & 1, a.status)) { ok = false; break; }
+                    if (!mbar_wait(&full[s], (it / C::STAGES) & 1, b.status)) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t sa = smem_u32(smem + s * C::STAGE), sb = sa + C::A_BYTES;
 #pragma unroll
@@ -253,7 +307,7 @@ __global__ void __launch_bounds__(192, 1)
                     }
                     umma_commit(&empty[s]);
                 }
-                umma_commit(&tfull[b]);
+                umma_commit(&tfull[bf]);
                 u = send;
             }
         }
@@ -262,39 +316,30 @@ __global__ void __launch_bounds__(192, 1)
         const int qd = warp & 3;
         const int r_in = qd * 32 + lane;
         const int et = threadIdx.x - 64;  // 0..127
+        const Loc first = locate(b, u0);
         uint32_t seg = 0;
-        const uint64_t first_row = u0 / a.KT;
         for (uint64_t u = u0; u < u1; ++seg) {
-            const uint64_t nt = u / a.KT;
-            const uint64_t rs = nt * a.KT, re = rs + a.KT;
+            const Loc l = locate(b, u);
+            const TcProblem &P = b.p[l.p];
+            const uint64_t rs = l.row_begin, re = rs + P.KT;
             const uint64_t send = umin64(u1, re);
             const bool full_row = (u == rs) && (send == re);
-            const uint32_t b = seg & 1, use = seg >> 1;
-            if (!mbar_wait(&tfull[b], use & 1, a.status)) break;
+            const uint32_t bf = seg & 1, use = seg >> 1;
+            if (!mbar_wait(&tfull[bf], use & 1, b.status)) break;
             tc_fence_after();
-            const int row = (int)(nt * 128) + r_in;
-            const uint32_t taddr = tmem + ((uint32_t)(qd * 32) << 16) + b * NPAD;
-            const int pslot = (nt == first_row) ? 0 : 1;
-            float *mypart = a.part + (((uint64_t)blockIdx.x * 2 + pslot) * 128 + r_in) * NPAD;
+            const int row = (int)(l.nt * 128) + r_in;
+            const uint32_t taddr = tmem + ((uint32_t)(qd * 32) << 16) + bf * NPAD;
+            const int pslot = (l.p == first.p && l.nt == first.nt) ? 0 : 1;
+            float *mypart = b.part + (((uint64_t)blockIdx.x * 2 + pslot) * 128 + r_in) * NPAD;
 #pragma unroll 1
             for (int c0 = 0; c0 < NPAD; c0 += 16) {
                 float v[16];
                 tmem_ld16(taddr + c0, v);
                 if (full_row) {
-                    if (row < a.N) {
-                        const float ws = FP8 ? a.w_scale[row] : 1.0f;
+                    if (row < P.N) {
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            const int m = c0 + j;
-                            if (m < a.M) {
-                                float o = v[j];
-                                if (FP8) o = o * ws * a.x_scale[m];
-                                if (a.relu) o = fmaxf(o, 0.0f);
-                                if (a.out_f32) reinterpret_cast<float *>(a.y)[(int64_t)m * a.N + row] = o;
-                                else reinterpret_cast<__nv_bfloat16 *>(a.y)[(int64_t)m * a.N + row] =
-                                    __float2bfloat16_rn(o);
-                            }
-                        }
+                        for (int j = 0; j < 16; ++j)
+                            if (c0 + j < b.M) store_out<FP8>(b, P, row, c0 + j, v[j]);
                     }
                 } else {
 #pragma unroll
@@ -304,55 +349,45 @@ __global__ void __launch_bounds__(192, 1)
                 }
             }
             tc_fence_before();
-            mbar_arrive(&tempty[b]);
+            mbar_arrive(&tempty[bf]);
             if (!full_row) {
                 // the last of the row's CTAs sums the pieces in CTA order
-                __threadfence();
                 asm volatile("bar.sync 1, 128;" ::: "memory");
                 const uint32_t c_first = cta_of_unit(rs, G, T), c_last = cta_of_unit(re - 1, G, T);
                 if (et == 0) {
+                    __threadfence();
                     const uint32_t pieces = c_last - c_first + 1;
-                    const uint32_t old = atomicAdd(a.rowcnt + nt, 1u);
+                    const uint32_t old = atomicAdd(P.rowcnt + l.nt, 1u);
+                    __threadfence();
                     *last_flag = (old == pieces - 1) ? 1u : 0u;
                 }
                 asm volatile("bar.sync 1, 128;" ::: "memory");
                 if (*last_flag) {
-                    __threadfence();
 #pragma unroll 1
                     for (int c0 = 0; c0 < NPAD; c0 += 16) {
                         float acc[16];
 #pragma unroll
                         for (int j = 0; j < 16; ++j) acc[j] = 0.0f;
                         for (uint32_t c = c_first; c <= c_last; ++c) {
-                            const uint64_t cu0 = (uint64_t)c * T / G;
-                            const int ps = (cu0 / a.KT == nt) ? 0 : 1;
-                            const float *p = a.part + (((uint64_t)c * 2 + ps) * 128 + r_in) * NPAD + c0;
+                            const Loc lc = locate(b, (uint64_t)c * T / G);
+                            const int ps = (lc.p == l.p && lc.nt == l.nt) ? 0 : 1;
+                            const float *pp = b.part + (((uint64_t)c * 2 + ps) * 128 + r_in) * NPAD + c0;
 #pragma unroll
                             for (int j = 0; j < 16; j += 4) {
-                                float4 t4 = __ldcg(reinterpret_cast<const float4 *>(p + j));
+                                float4 t4 = __ldcg(reinterpret_cast<const float4 *>(pp + j));
                                 acc[j] += t4.x;
                                 acc[j + 1] += t4.y;
                                 acc[j + 2] += t4.z;
                                 acc[j + 3] += t4.w;
                             }
                         }
-                        if (row < a.N) {
-                            const float ws = FP8 ? a.w_scale[row] : 1.0f;
+                        if (row < P.N) {
 #pragma unroll
-                            for (int j = 0; j < 16; ++j) {
-                                const int m = c0 + j;
-                                if (m < a.M) {
-                                    float o = acc[j];
-                                    if (FP8) o = o * ws * a.x_scale[m];
-                                    if (a.relu) o = fmaxf(o, 0.0f);
-                                    if (a.out_f32) reinterpret_cast<float *>(a.y)[(int64_t)m * a.N + row] = o;
-                                    else reinterpret_cast<__nv_bfloat16 *>(a.y)[(int64_t)m * a.N + row] =
-                                        __float2bfloat16_rn(o);
-                                }
-                            }
+                            for (int j = 0; j < 16; ++j)
+                                if (c0 + j < b.M) store_out<FP8>(b, P, row, c0 + j, acc[j]);
                         }
                     }
-                    if (et == 0) a.rowcnt[nt] = 0;  // ready for the next launch
+                    if (et == 0) P.rowcnt[l.nt] = 0;  // ready for the next launch
                 }
             }
             u = send;
@@ -367,24 +402,26 @@ __global__ void __launch_bounds__(192, 1)
 }
 
 template <bool FP8, int NPAD>
-static cloak_status launch_tc(cloak_ctx *ctx, const CUtensorMap &tw, const void *x, int K, int M,
-                              TcArgs a, cudaStream_t s) {
+static cloak_status launch_tc(cloak_ctx *ctx, const CUtensorMap &tw, const void *const *xs,
+                              TcBatch &b, cudaStream_t s) {
     using C = TcCfg<FP8, NPAD>;
-    static bool attr_set = false;  // per instantiation; set once per process
+    static bool attr_set = false;  // per instantiation; once per process
     if (!attr_set) {
         CLOAK_CUDA(ctx, cudaFuncSetAttribute(k_linear_tc<FP8, NPAD>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
         attr_set = true;
     }
-    CUtensorMap tx;
+    TxMaps tx;
     const int es = FP8 ? 1 : 2;
-    if (!encode_tmap_2d(&tx, FP8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
-                        x, (uint64_t)K, (uint64_t)M, (uint64_t)K * es, 128 / es, NPAD)) {
-        ctx->last_err = "cuTensorMapEncodeTiled failed for x";
-        return CLOAK_E_CUDA;
+    for (int p = 0; p < b.np; ++p) {
+        if (!encode_tmap_2d(&tx.m[p], FP8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                            xs[p], (uint64_t)b.p[p].K, (uint64_t)b.M, (uint64_t)b.p[p].K * es,
+                            128 / es, NPAD)) {
+            ctx->last_err = "cuTensorMapEncodeTiled failed for x";
+            return CLOAK_E_CUDA;
+        }
     }
-    const uint64_t T = (uint64_t)a.NT * a.KT;
-    const uint32_t grid = (uint32_t)std::min<uint64_t>(T, (uint64_t)ctx->sm_count);
+    const uint32_t grid = (uint32_t)std::min<uint64_t>(b.total, (uint64_t)ctx->sm_count);
     const size_t need = (size_t)grid * 2 * 128 * NPAD;
     if (need > ctx->part_cap) {
         if (ctx->d_part) CLOAK_CUDA(ctx, cudaFree(ctx->d_part));
@@ -392,82 +429,106 @@ static cloak_status launch_tc(cloak_ctx *ctx, const CUtensorMap &tw, const void 
         CLOAK_CUDA(ctx, cudaMalloc(&ctx->d_part, need * sizeof(float)));
         ctx->part_cap = need;
     }
-    a.part = ctx->d_part;
-    k_linear_tc<FP8, NPAD><<<grid, 192, C::SMEM, s>>>(tw, tx, a);
+    b.part = ctx->d_part;
+    k_linear_tc<FP8, NPAD><<<grid, 192, C::SMEM, s>>>(tw, tx, b);
     CLOAK_LAUNCHED(ctx);
     return CLOAK_OK;
 }
 
 template <bool FP8>
-static cloak_status dispatch_tc(cloak_ctx *ctx, const CUtensorMap &tw, const void *x, int K, int M,
-                                const TcArgs &a, cudaStream_t s) {
-    if (M <= 16) return launch_tc<FP8, 16>(ctx, tw, x, K, M, a, s);
-    if (M <= 32) return launch_tc<FP8, 32>(ctx, tw, x, K, M, a, s);
-    if (M <= 64) return launch_tc<FP8, 64>(ctx, tw, x, K, M, a, s);
-    if (M <= 128) return launch_tc<FP8, 128>(ctx, tw, x, K, M, a, s);
-    return launch_tc<FP8, 256>(ctx, tw, x, K, M, a, s);
+static cloak_status dispatch_tc(cloak_ctx *ctx, const CUtensorMap &tw, const void *const *xs,
+                                TcBatch &b, cudaStream_t s) {
+    if (b.M <= 16) return launch_tc<FP8, 16>(ctx, tw, xs, b, s);
+    if (b.M <= 32) return launch_tc<FP8, 32>(ctx, tw, xs, b, s);
+    if (b.M <= 64) return launch_tc<FP8, 64>(ctx, tw, xs, b, s);
+    if (b.M <= 128) return launch_tc<FP8, 128>(ctx, tw, xs, b, s);
+    return launch_tc<FP8, 256>(ctx, tw, xs, b, s);
 }
 
-cloak_status linear_run(cloak_ctx *ctx, int t, const void *x, void *y, int M, int out_dtype,
-                        int flags, cudaStream_t s) {
+cloak_status linear_batch_run(cloak_ctx *ctx, int n, const int32_t *tensors, const void *const *xs,
+                              void *const *ys, int M, int out_dtype, int flags, cudaStream_t s) {
     CLOAK_CUDA(ctx, cudaSetDevice(ctx->device));
-    const TensorInfo &ti = ctx->info[t];
     const bool unc = flags & CLOAK_LINEAR_UNCLOAKED;
     const int relu = (flags & CLOAK_LINEAR_RELU) ? 1 : 0;
-    const uint32_t base = ctx->h_tensor_base[t];
-    const uint8_t *arena = unc ? ctx->twin : ctx->arena;
     const uint32_t *slot_of = unc ? nullptr : ctx->d_tile_slot;
     const int oes = out_dtype == CLOAK_OUT_F32 ? 4 : 2;
     if (ctx->dtype == CLOAK_F32) {
         if (ctx->tile_r != 64 || ctx->tile_c != 64) return CLOAK_E_UNSUPPORTED;
-        k_linear_f32<8><<<ti.nt, 256, 0, s>>>(arena, slot_of, base, ti.n, ti.k, ti.kt,
-                                              (const float *)x, (float *)y, M,
-                                              out_dtype == CLOAK_OUT_F32, relu);
-        CLOAK_LAUNCHED(ctx);
+        const uint8_t *arena = unc ? ctx->twin : ctx->arena;
+        for (int p = 0; p < n; ++p) {
+            const TensorInfo &ti = ctx->info[tensors[p]];
+            k_linear_f32<8><<<ti.nt, 256, 0, s>>>(arena, slot_of, ctx->h_tensor_base[tensors[p]], ti.n,
+                                                  ti.k, ti.kt, (const float *)xs[p], (float *)ys[p], M,
+                                                  out_dtype == CLOAK_OUT_F32, relu);
+            CLOAK_LAUNCHED(ctx);
+        }
         return CLOAK_OK;
     }
     const bool fp8 = ctx->dtype == CLOAK_E4M3;
     const CUtensorMap &tw = unc ? ctx->tmap_twin : ctx->tmap_arena;
-    const int ies = 2;  // activations are BF16
+    if (fp8) {
+        size_t qb = 0;
+        for (int p = 0; p < n; ++p) qb += (size_t)std::min(M, 256) * ctx->info[tensors[p]].k;
+        if (qb > ctx->xq_cap) {
+            if (ctx->d_xq) CLOAK_CUDA(ctx, cudaFree(ctx->d_xq));
+            ctx->d_xq = nullptr;
+            CLOAK_CUDA(ctx, cudaMalloc(&ctx->d_xq, qb));
+            ctx->xq_cap = qb;
+        }
+        if (!ctx->d_xs) CLOAK_CUDA(ctx, cudaMalloc(&ctx->d_xs, MAXP * 256 * sizeof(float)));
+    }
     for (int m0 = 0; m0 < M; m0 += 256) {
         const int mb = std::min(256, M - m0);
-        TcArgs a{};
-        a.slot_of = slot_of;
-        a.base = base;
-        a.N = ti.n;
-        a.K = ti.k;
-        a.NT = ti.nt;
-        a.KT = ti.kt;
-        a.M = mb;
-        a.y = (uint8_t *)y + (size_t)m0 * ti.n * oes;
-        a.out_f32 = out_dtype == CLOAK_OUT_F32;
-        a.relu = relu;
-        a.rowcnt = ctx->d_rowcnt + ti.row_off;
-        a.status = ctx->d_status;
-        const uint8_t *xm = (const uint8_t *)x + (size_t)m0 * ti.k * ies;
-        cloak_status rc;
-        if (fp8) {
-            const size_t qb = (size_t)mb * ti.k;
-            if (qb > ctx->xq_cap) {
-                if (ctx->d_xq) CLOAK_CUDA(ctx, cudaFree(ctx->d_xq));
-                if (ctx->d_xs) CLOAK_CUDA(ctx, cudaFree(ctx->d_xs));
-                ctx->d_xq = nullptr;
-                ctx->d_xs = nullptr;
-                CLOAK_CUDA(ctx, cudaMalloc(&ctx->d_xq, qb));
-                CLOAK_CUDA(ctx, cudaMalloc(&ctx->d_xs, 256 * sizeof(float)));
-                ctx->xq_cap = qb;
+        TcBatch b{};
+        b.slot_of = slot_of;
+        b.np = n;
+        b.M = mb;
+        b.out_f32 = out_dtype == CLOAK_OUT_F32;
+        b.relu = relu;
+        b.status = ctx->d_status;
+        const void *xm[MAXP];
+        uint64_t u = 0;
+        size_t qoff = 0;
+        for (int p = 0; p < n; ++p) {
+            const int t = tensors[p];
+            const TensorInfo &ti = ctx->info[t];
+            TcProblem &P = b.p[p];
+            P.u_begin = u;
+            P.base = ctx->h_tensor_base[t];
+            P.N = ti.n;
+            P.K = ti.k;
+            P.NT = ti.nt;
+            P.KT = ti.kt;
+            P.y = (uint8_t *)ys[p] + (size_t)m0 * ti.n * oes;
+            P.rowcnt = ctx->d_rowcnt + ti.row_off;
+            u += (uint64_t)ti.nt * ti.kt;
+            const uint8_t *x = (const uint8_t *)xs[p] + (size_t)m0 * ti.k * 2;  // BF16 activations
+            if (fp8) {
+                uint8_t *q = ctx->d_xq + qoff;
+                float *sc = ctx->d_xs + p * 256;
+                qoff += (size_t)mb * ti.k;
+                k_quant_rows<<<mb, 256, 0, s>>>((const __nv_bfloat16 *)x, ti.k, q, sc);
+                CLOAK_LAUNCHED(ctx);
+                P.w_scale = ctx->d_scales + ti.scale_off;
+                P.x_scale = sc;
+                xm[p] = q;
+            } else {
+                xm[p] = x;
             }
-            k_quant_rows<<<mb, 256, 0, s>>>((const __nv_bfloat16 *)xm, ti.k, ctx->d_xq, ctx->d_xs);
-            CLOAK_LAUNCHED(ctx);
-            a.w_scale = ctx->d_scales + ti.scale_off;
-            a.x_scale = ctx->d_xs;
-            rc = dispatch_tc<true>(ctx, tw, ctx->d_xq, ti.k, mb, a, s);
-        } else {
-            rc = dispatch_tc<false>(ctx, tw, xm, ti.k, mb, a, s);
         }
+        b.total = u;
+        cloak_status rc = fp8 ? dispatch_tc<true>(ctx, tw, xm, b, s) : dispatch_tc<false>(ctx, tw, xm, b, s);
         if (rc) return rc;
     }
     return CLOAK_OK;
+}
+
+cloak_status linear_run(cloak_ctx *ctx, int t, const void *x, void *y, int M, int out_dtype,
+                        int flags, cudaStream_t s) {
+    const int32_t tt[1] = {t};
+    const void *xs[1] = {x};
+    void *ys[1] = {y};
+    return linear_batch_run(ctx, 1, tt, xs, ys, M, out_dtype, flags, s);
 }
 
 }  // namespace cloak

@@ -150,3 +150,54 @@ def test_bad_calls_return_errors(cloak_lib):
         cloak_lib.cloak_linear(cm.ctx, 99, x.data_ptr(), x.data_ptr(), 2, 0)
     assert cm.device_status() == 0
     cm.close()
+
+
+@pytest.mark.parametrize("M", [1, 8, 64])
+def test_batched_layer_launch(cloak_lib, M):
+    """All seven linears of a decoder layer in one launch (one split over
+    their concatenated tiles): each output within tolerance of the oracle,
+    cloaked and uncloaked batches bit-identical."""
+    m = synth.small_decoder(2, synth.DT_BF16, d_model=384, n_heads=6, n_kv_heads=2, d_ff=200,
+                            spare_pages=5)
+    cm, om, tb, arena, scales, Ws = place_both(cloak_lib, m, key=0x77)
+    for layer in range(2):
+        ts = [i for i, t in enumerate(m.tensors) if t.layer == layer]
+        xs_h = [synth.activations_host(M, m.tensors[t].k, seed=50 + t) for t in ts]
+        xs = [x_device(m, x) for x in xs_h]
+        ys = cm.linear_batch(ts, xs, out_dtype=cloak_lib.OUT_F32)
+        yu = cm.linear_batch(ts, xs, out_dtype=cloak_lib.OUT_F32, uncloaked=True)
+        torch.cuda.synchronize()
+        for t, x, y, u in zip(ts, xs_h, ys, yu):
+            ref = O.cloaked_linear(om, tb, t, arena, x)
+            assert O.relative_error(y.cpu().numpy(), ref) <= 1e-2
+            assert torch.equal(y, u)
+    cm.close()
+
+
+def test_batched_fp8_launch(cloak_lib):
+    m = synth.small_decoder(1, synth.DT_E4M3, page_bytes=2 * 128 * 128, d_model=384, n_heads=6,
+                            n_kv_heads=2, d_ff=256)
+    cm, om, tb, arena, scales, Ws = place_both(cloak_lib, m, key=0x78)
+    ts = list(range(len(m.tensors)))
+    xs_h = [synth.activations_host(5, m.tensors[t].k, seed=t) for t in ts]
+    ys = cm.linear_batch(ts, [x_device(m, x) for x in xs_h], out_dtype=cloak_lib.OUT_F32)
+    torch.cuda.synchronize()
+    for t, x, y in zip(ts, xs_h, ys):
+        ref = O.cloaked_linear(om, tb, t, arena, x, scales[t])
+        assert O.relative_error(y.cpu().numpy(), ref) <= 1e-5
+    cm.close()
+
+
+def test_batched_full_layer(cloak_lib):
+    m = synth.llama7b_layer(1)
+    cm, om, tb, arena, scales, Ws = place_both(cloak_lib, m, key=0x1234)
+    ts = list(range(7))
+    xs_h = [synth.activations_host(8, m.tensors[t].k, seed=200 + t) for t in ts]
+    xs = [x_device(m, x) for x in xs_h]
+    ys = cm.linear_batch(ts, xs, out_dtype=cloak_lib.OUT_F32)
+    yu = cm.linear_batch(ts, xs, out_dtype=cloak_lib.OUT_F32, uncloaked=True)
+    torch.cuda.synchronize()
+    for t, x, y, u in zip(ts, xs_h, ys, yu):
+        assert O.relative_error(y.cpu().numpy(), O.cloaked_linear(om, tb, t, arena, x)) <= 1e-2
+        assert torch.equal(y, u)
+    cm.close()
