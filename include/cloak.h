@@ -190,6 +190,28 @@ CLOAK_API cloak_status cloak_linear_batch(cloak_ctx *ctx, int32_t n, const int32
 CLOAK_API cloak_status cloak_linear_host(cloak_ctx *ctx, int32_t tensor, const void *x_host, void *y_host,
                                int32_t M, int32_t out_dtype, int32_t flags, void *stream);
 
+/* cloak_linear for callers that cannot allocate device memory while they
+ * run: code inside CUDA stream capture (an allocation there breaks the
+ * capture), serving loops under a memory pool that owns every byte, or
+ * real-time paths where cudaMalloc's synchronisation is not allowed.
+ * cloak_linear itself may grow its context-owned scratch with cudaMalloc; this
+ * call never calls cudaMalloc, cudaFree or any allocating routine. Its scratch
+ * (split-K partial sums and tile-row counters) is one fixed 5 MiB + 16 KiB
+ * device array inside the library, held on every GPU that loads it until the
+ * process exits. The paper has no counterpart: this is a deployment aid.
+ *   Limits: BF16 models only (else CLOAK_E_UNSUPPORTED); 1 <= M <= 32 and at
+ *   most 4096 tile rows per tensor (else CLOAK_E_INVAL, message in
+ *   cloak_last_error).
+ *   The first call on a device looks up the array's device address and zeroes
+ *   its counters (synchronous); make that first call before any stream
+ *   capture. Every call shares the one array and clears the counters it uses
+ *   on `stream`; calls that overlap on the GPU (other streams, other contexts)
+ *   race on it and must be ordered by the caller.
+ * Results equal cloak_linear's for the same arguments. */
+CLOAK_API cloak_status cloak_linear_noalloc(cloak_ctx *ctx, int32_t tensor, const void *x_dev,
+                                            void *y_dev, int32_t M, int32_t out_dtype,
+                                            int32_t flags, void *stream);
+
 /* Re-key (periodic re-randomisation, Section 4.2 and Figure 7): draw the page
  * map of (key, new_epoch) and move every placed page to its new physical page
  * in place, through a small staging pool, so the arena ends bit-identical to

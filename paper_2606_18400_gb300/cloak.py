@@ -65,6 +65,7 @@ SIGNATURES = [
     ("cloak_linear_batch", _i32, [_vp, _i32, C.POINTER(_i32), C.POINTER(_vp), C.POINTER(_vp), _i32,
                                   _i32, _i32, _vp]),
     ("cloak_linear_host", _i32, [_vp, _i32, _vp, _vp, _i32, _i32, _i32, _vp]),
+    ("cloak_linear_noalloc", _i32, [_vp, _i32, _vp, _vp, _i32, _i32, _i32, _vp]),
     ("cloak_rekey", _i32, [_vp, _u64, _u32, _vp]),
     ("cloak_device_status", _i32, [_vp]),
     ("cloak_last_error", C.c_char_p, [_vp]),
@@ -178,6 +179,12 @@ def cloak_linear_host(ctx, tensor: int, x_host: int, y_host: int, M: int, out_dt
                       flags: int = 0, stream=None):
     _check("cloak_linear_host", load().cloak_linear_host(ctx, tensor, x_host, y_host, M, out_dtype,
                                                          flags, _stream(stream)), ctx)
+
+
+def cloak_linear_noalloc(ctx, tensor: int, x_dev: int, y_dev: int, M: int, out_dtype: int,
+                         flags: int = 0, stream=None):
+    _check("cloak_linear_noalloc", load().cloak_linear_noalloc(ctx, tensor, x_dev, y_dev, M, out_dtype,
+                                                               flags, _stream(stream)), ctx)
 
 
 def cloak_rekey(ctx, key: int, new_epoch: int, stream=None):

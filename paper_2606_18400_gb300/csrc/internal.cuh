@@ -134,5 +134,8 @@ cloak_status linear_run(cloak_ctx *ctx, int t, const void *x, void *y, int M, in
                         int flags, cudaStream_t s);
 cloak_status linear_batch_run(cloak_ctx *ctx, int n, const int32_t *tensors, const void *const *xs,
                               void *const *ys, int M, int out_dtype, int flags, cudaStream_t s);
+cloak_status linear_run_given_scratch(cloak_ctx *ctx, int t, const void *x, void *y, int M,
+                                      int out_dtype, int flags, float *part, size_t part_floats,
+                                      uint32_t *rowcnt, uint32_t max_grid, cudaStream_t s);
 
 }  // namespace cloak
