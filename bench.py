@@ -211,6 +211,123 @@ def traffic_record(kernel_src):
     return rec.get("dram_bytes_per_step") if rec.get("source_sha") == h else None
 
 
+def bench_extras(cloak, synth, torch, dev, stream, key, steps):
+    """Other rows of the hot path, each on its own context: BF16 prefill of the
+    7B-class layer (M = 512, 2048), the FP8 GQA layer (decode M = 1 and
+    prefill M = 2048), and the in-place re-key of the 32-layer 12.95 GB stack."""
+    out = {}
+
+    def timed(fn, K, W=3):
+        for _ in range(W):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(K):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / K
+
+    def graph(fn):
+        fn()
+        fn()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            fn()
+        return g
+
+    def layer_run(cm, model, M, seed0):
+        T = len(model.tensors)
+        xs = [torch.from_numpy(synth.activations_host(M, t.k, seed=seed0 + i)).cuda().to(torch.bfloat16)
+              for i, t in enumerate(model.tensors)]
+        ys = [torch.empty((M, t.n), dtype=torch.bfloat16, device="cuda") for t in model.tensors]
+        res = {}
+        for name, flags in (("cloaked", 0), ("uncloaked", cloak.LINEAR_UNCLOAKED)):
+            def fn(flags=flags):
+                cloak.cloak_linear_batch(cm.ctx, list(range(T)), [x.data_ptr() for x in xs],
+                                         [y.data_ptr() for y in ys], M, cloak.OUT_BF16, flags,
+                                         stream.cuda_stream)
+            g = graph(fn)
+            res[name] = timed(g.replay, max(10, steps // 4))
+            del g
+        return res
+
+    # BF16 prefill, 7B-class layer
+    model = synth.llama7b_layer(1)
+    cm = cloak.CloakModel(model, device=dev, twin=True)
+    cm.keygen(key, 0)
+    for t in range(len(model.tensors)):
+        cm.shuffle(t, synth.weights_device(model, t, seed=0))
+    flops1 = 2 * sum(t.n * t.k for t in model.tensors)
+    pre = {}
+    for M in (512, 2048):
+        r = layer_run(cm, model, M, 300)
+        pre[str(M)] = {"cloaked_tflops": round(flops1 * M / (r["cloaked"] / 1e3) / 1e12, 1),
+                       "uncloaked_tflops": round(flops1 * M / (r["uncloaked"] / 1e3) / 1e12, 1),
+                       "cloaked_ms": round(r["cloaked"], 4), "uncloaked_ms": round(r["uncloaked"], 4)}
+    out["prefill_bf16_llama7b_layer"] = pre
+    cm.close()
+    torch.cuda.empty_cache()
+
+    # FP8 GQA layer (d 3584, 28/4 heads, MLP 18944), E4M3 + FP32 row scales
+    model = synth.gqa28_fp8(1)
+    cm = cloak.CloakModel(model, device=dev, twin=True)
+    cm.keygen(key, 0)
+    for t in range(len(model.tensors)):
+        cm.shuffle(t, synth.weights_device(model, t, seed=7))
+    wbytes = sum(t.n * t.k for t in model.tensors)
+    f8 = {}
+    r = layer_run(cm, model, 1, 400)
+    b1 = wbytes + 4 * cm.G + sum(2 * t.k + 2 * t.n + 4 * t.n for t in model.tensors)  # x, y, row scales
+    f8["decode_M1"] = {"cloaked_gbs": round(b1 / (r["cloaked"] / 1e3) / 1e9, 1),
+                       "uncloaked_gbs": round(b1 / (r["uncloaked"] / 1e3) / 1e9, 1),
+                       "cloaked_us": round(r["cloaked"] * 1e3, 2), "weight_bytes": wbytes}
+    r = layer_run(cm, model, 2048, 500)
+    f8["prefill_M2048"] = {"cloaked_tflops": round(2 * wbytes * 2048 / (r["cloaked"] / 1e3) / 1e12, 1),
+                           "uncloaked_tflops": round(2 * wbytes * 2048 / (r["uncloaked"] / 1e3) / 1e12, 1)}
+    out["fp8_gqa3584_layer"] = f8
+    cm.close()
+    torch.cuda.empty_cache()
+
+    # re-key of the whole 32-layer BF16 stack (12.95 GB, 6,176 pages + 64 spare).
+    # The arena holds random bytes: a page copy costs the same whatever it holds.
+    model = synth.llama7b_layer(32)
+    cm = cloak.CloakModel(model, device=dev, twin=False)
+    t0 = time.perf_counter()
+    cm.keygen(key, 0)
+    kg_ms = (time.perf_counter() - t0) * 1e3
+    arena = cm.arena_bytes(0)
+    g = torch.Generator(device=f"cuda:{dev}")
+    g.manual_seed(11)
+    for off in range(0, arena.numel(), 1 << 30):
+        seg = arena[off:off + (1 << 30)]
+        seg.copy_(torch.randint(0, 256, seg.shape, dtype=torch.uint8, device=seg.device, generator=g))
+    del arena
+    torch.cuda.synchronize()
+    ts = []
+    for e in range(1, 5):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        a.record()
+        cm.rekey(key, e)
+        b.record()
+        torch.cuda.synchronize()
+        ts.append((a.elapsed_time(b), (time.perf_counter() - t0) * 1e3))
+    moved = cm.NP * model.page_bytes
+    med = statistics.median(x[0] for x in ts)
+    out["rekey_llama7b_32L"] = {"ms": round(med, 3), "moved_bytes": moved,
+                                "gbs_rw": round(2 * moved / (med / 1e3) / 1e9, 1),
+                                "host_ms": round(statistics.median(x[1] for x in ts), 3),
+                                "keygen_ms": round(kg_ms, 2), "pages": cm.NP, "spare": model.spare_pages,
+                                "staging_pages": min(256, max(2, cm.NPS // 32))}
+    assert cm.device_status() == 0
+    cm.close()
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_cloak(args):
     import torch
     from paper_2606_18400_gb300 import cloak, synth
@@ -372,8 +489,11 @@ def run_cloak(args):
         rk.append(a.elapsed_time(b))
     rekey_ms = statistics.median(rk)
     moved = cm.NP * model.page_bytes
-    clk = clocks.stop()
     status = cm.device_status()
+    cm.close()
+    extras = None if args.no_extras else bench_extras(cloak, synth, torch, dev, stream, KEY + rank,
+                                                      args.steps)
+    clk = clocks.stop()
 
     if rank == 0:
         cpu = None
@@ -411,9 +531,9 @@ def run_cloak(args):
                       "gbs_rw": round(2 * moved / (rekey_ms / 1e3) / 1e9, 1)},
             "keygen_ms": round(keygen_ms, 2), "shuffle_gbs": round(shuffle_gbs, 1),
             "device_status": status,
+            "extras": extras,
         }
         print(json.dumps(line), flush=True)
-    cm.close()
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -428,6 +548,7 @@ def main():
     ap.add_argument("--M", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
