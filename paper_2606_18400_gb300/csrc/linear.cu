@@ -98,10 +98,20 @@ __global__ void __launch_bounds__(256) k_linear_f32(const uint8_t *arena, const 
 
 // --------------------------------------------------- activation quantiser
 
-// one block per row: s = amax/448 (1 for a zero row), q = E4M3(x / s)
-__global__ void k_quant_rows(const __nv_bfloat16 *x, int K, uint8_t *q, float *s) {
+// per row: s = amax/448 (1 for a zero row), q = E4M3(x / s) (FP32 quotient)
+struct QuantJobs {
+    const __nv_bfloat16 *x[8];
+    uint8_t *q[8];
+    float *s[8];
+    int K[8];
+};
+
+// one launch for every problem of a batch: block (r, p) quantises row r of x_p
+__global__ void k_quant_rows_multi(QuantJobs j) {
+    const int p = blockIdx.y;
     const int64_t r = blockIdx.x;
-    const __nv_bfloat16 *xr = x + r * K;
+    const int K = j.K[p];
+    const __nv_bfloat16 *xr = j.x[p] + r * K;
     float m = 0.0f;
     for (int c = threadIdx.x; c < K; c += blockDim.x) m = fmaxf(m, fabsf(__bfloat162float(xr[c])));
     __shared__ float red[32];
@@ -114,14 +124,15 @@ __global__ void k_quant_rows(const __nv_bfloat16 *x, int K, uint8_t *q, float *s
         for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
         if (threadIdx.x == 0) {
             sc = m > 0.0f ? __fdiv_rn(m, 448.0f) : 1.0f;
-            s[r] = sc;
+            j.s[p][r] = sc;
         }
     }
     __syncthreads();
     const float d = sc;
+    uint8_t *qr = j.q[p] + r * K;
     for (int c = threadIdx.x; c < K; c += blockDim.x)
-        q[r * K + c] = (uint8_t)__nv_cvt_float_to_fp8(__fdiv_rn(__bfloat162float(xr[c]), d),
-                                                      __NV_SATFINITE, __NV_E4M3);
+        qr[c] = (uint8_t)__nv_cvt_float_to_fp8(__fdiv_rn(__bfloat162float(xr[c]), d), __NV_SATFINITE,
+                                                __NV_E4M3);
 }
 
 // ------------------------------------------------------ tensor-core path
@@ -189,6 +200,16 @@ __device__ __forceinline__ Loc locate(const TcBatch &b, uint64_t u) {
     return l;
 }
 
+// arena slot of unit u (0 past the end): gather-table read, or the tile
+// index itself for the uncloaked twin
+__device__ __forceinline__ uint32_t slot_for(const TcBatch &b, uint64_t u, uint64_t u1) {
+    if (u >= u1) return 0;
+    int p = 0;
+    while (p + 1 < b.np && u >= b.p[p + 1].u_begin) ++p;
+    const uint32_t g = b.p[p].base + (uint32_t)(u - b.p[p].u_begin);
+    return b.slot_of ? __ldg(b.slot_of + g) : g;
+}
+
 template <bool FP8>
 __device__ __forceinline__ void store_out(const TcBatch &b, const TcProblem &P, int row, int m,
                                           float v) {
@@ -240,18 +261,28 @@ __global__ void __launch_bounds__(192, 1)
     const uint32_t tmem = *tmem_slot;
 
     if (warp == 0) {
-        if (lane == 0) {
-            const uint64_t pol_w = policy_evict_first(), pol_x = policy_evict_last();
-            Loc l = locate(b, u0);
-            uint32_t it = 0;
-            for (uint64_t u = u0; u < u1; ++u, ++it) {
-                const int s = it % C::STAGES;
-                const uint32_t ph = (it / C::STAGES) & 1;
-                if (it >= (uint32_t)C::STAGES && !mbar_wait(&empty[s], ph ^ 1, b.status)) break;
-                const TcProblem &P = b.p[l.p];
+        // TMA producer. The whole warp walks the units so the gather-table
+        // entries are fetched 32 at a time, one chunk ahead (coalesced, off the
+        // critical path); lane 0 waits on the ring and issues the copies.
+        const uint64_t pol_w = policy_evict_first(), pol_x = policy_evict_last();
+        Loc l = locate(b, u0);
+        uint32_t cur = slot_for(b, u0 + lane, u1), nxt = slot_for(b, u0 + 32 + lane, u1);
+        uint32_t it = 0;
+        for (uint64_t u = u0; u < u1; ++u, ++it) {
+            const uint32_t j = (uint32_t)((u - u0) & 31);
+            if (j == 0 && u > u0) {
+                cur = nxt;
+                nxt = slot_for(b, u + 32 + lane, u1);
+            }
+            const uint32_t slot = __shfl_sync(0xffffffffu, cur, j);
+            const int s = it % C::STAGES;
+            const uint32_t ph = (it / C::STAGES) & 1;
+            bool ok = true;
+            if (lane == 0 && it >= (uint32_t)C::STAGES) ok = mbar_wait(&empty[s], ph ^ 1, b.status);
+            if (!__shfl_sync(0xffffffffu, (int)ok, 0)) break;
+            const TcProblem &P = b.p[l.p];
+            if (lane == 0) {
                 mbar_expect_tx(&full[s], C::STAGE);
-                const uint32_t g = P.base + (uint32_t)(u - P.u_begin);
-                const uint32_t slot = b.slot_of ? __ldg(b.slot_of + g) : g;
                 const int32_t row = (int32_t)(slot * 128u);
                 const int32_t kc = (int32_t)l.kt * 128;
                 uint8_t *sa = smem + s * C::STAGE, *sb = sa + C::A_BYTES;
@@ -265,13 +296,13 @@ __global__ void __launch_bounds__(192, 1)
                     tma_load_2d_hint(sb, xm, &full[s], kc, 0, pol_x);
                     tma_load_2d_hint(sb + C::B_BYTES / 2, xm, &full[s], kc + 64, 0, pol_x);
                 }
-                // advance (problem, row, column)
-                if (++l.kt == (uint32_t)P.KT) {
-                    l.kt = 0;
-                    if (++l.nt == (uint32_t)P.NT) {
-                        l.nt = 0;
-                        ++l.p;
-                    }
+            }
+            // advance (problem, row, column)
+            if (++l.kt == (uint32_t)P.KT) {
+                l.kt = 0;
+                if (++l.nt == (uint32_t)P.NT) {
+                    l.nt = 0;
+                    ++l.p;
                 }
             }
         }
@@ -489,6 +520,7 @@ cloak_status linear_batch_run(cloak_ctx *ctx, int n, const int32_t *tensors, con
         const void *xm[MAXP];
         uint64_t u = 0;
         size_t qoff = 0;
+        QuantJobs qj{};
         for (int p = 0; p < n; ++p) {
             const int t = tensors[p];
             const TensorInfo &ti = ctx->info[t];
@@ -507,8 +539,10 @@ cloak_status linear_batch_run(cloak_ctx *ctx, int n, const int32_t *tensors, con
                 uint8_t *q = ctx->d_xq + qoff;
                 float *sc = ctx->d_xs + p * 256;
                 qoff += (size_t)mb * ti.k;
-                k_quant_rows<<<mb, 256, 0, s>>>((const __nv_bfloat16 *)x, ti.k, q, sc);
-                CLOAK_LAUNCHED(ctx);
+                qj.x[p] = (const __nv_bfloat16 *)x;
+                qj.q[p] = q;
+                qj.s[p] = sc;
+                qj.K[p] = ti.k;
                 P.w_scale = ctx->d_scales + ti.scale_off;
                 P.x_scale = sc;
                 xm[p] = q;
@@ -517,6 +551,10 @@ cloak_status linear_batch_run(cloak_ctx *ctx, int n, const int32_t *tensors, con
             }
         }
         b.total = u;
+        if (fp8) {
+            k_quant_rows_multi<<<dim3(mb, n), 256, 0, s>>>(qj);
+            CLOAK_LAUNCHED(ctx);
+        }
         cloak_status rc = fp8 ? dispatch_tc<true>(ctx, tw, xm, b, s) : dispatch_tc<false>(ctx, tw, xm, b, s);
         if (rc) return rc;
     }
