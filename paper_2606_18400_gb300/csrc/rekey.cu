@@ -182,6 +182,240 @@ __global__ void k_rekey_plan(PlanArgs a) {
     plan[3] = passes;
 }
 
+// Parallel planner (one CTA of 1024 threads, arrays in global scratch).
+// Each move source x gets its component (its chain's start, or the smallest
+// page of its cycle) and its position i from that start by pointer jumping
+// backwards along the moves: a node's record covers up to 2^r nodes behind
+// it (count, last node, smallest page and the distance to it). With m moves
+// in the component, x's move is e_k, k = m - i: wave 1 + (k-1) % L, segment
+// (k-1) / L. A pass is [staging ops][wave 1: one slot per segment]...[wave
+// plen]; every op's slot is a closed form, and short segments leave holes
+// that the copy kernel skips.
+constexpr uint32_t PAR_SCRATCH_ARRAYS = 21;  // words of scratch = 21 * NPS + 64
+
+struct ParPlan {
+    const uint32_t *old_pa, *new_pa;
+    uint32_t NP, NPS, cap_stage, max_ops;
+    uint32_t *plan;
+    uint32_t *w;
+};
+
+__global__ void __launch_bounds__(1024) k_rekey_plan_par(ParPlan a) {
+    const uint32_t N = a.NPS, tid = threadIdx.x, nth = blockDim.x;
+    uint32_t *dst_of = a.w, *src_of = a.w + N;
+    uint32_t *jp[2] = {a.w + 2 * N, a.w + 3 * N}, *jl[2] = {a.w + 4 * N, a.w + 5 * N},
+             *jm[2] = {a.w + 6 * N, a.w + 7 * N}, *jd[2] = {a.w + 8 * N, a.w + 9 * N},
+             *ja[2] = {a.w + 10 * N, a.w + 11 * N};
+    uint32_t *msize = a.w + 12 * N, *head = a.w + 13 * N, *cinfo = a.w + 14 * N,
+             *c_pass = a.w + 15 * N, *c_seg = a.w + 16 * N, *c_stg = a.w + 17 * N,
+             *pass_rec = a.w + 18 * N, *misc = a.w + 21 * N;
+    uint32_t *plan = a.plan;
+    __shared__ uint32_t s_scan[1024];
+    __shared__ uint64_t s_red[32];
+    for (uint32_t p = tid; p < N; p += nth) {
+        dst_of[p] = NONE;
+        src_of[p] = NONE;
+        msize[p] = 0;
+        head[p] = 0;
+    }
+    if (tid < PLAN_HDR) plan[tid] = 0;
+    __syncthreads();
+    for (uint32_t vp = tid; vp < a.NP; vp += nth) {
+        const uint32_t o = a.old_pa[vp], n = a.new_pa[vp];
+        if (o != n) {
+            dst_of[o] = n;
+            src_of[n] = o;
+        }
+    }
+    __syncthreads();
+    for (uint32_t x = tid; x < N; x += nth) {
+        jp[0][x] = src_of[x];
+        jl[0][x] = 1;
+        jm[0][x] = x;
+        jd[0][x] = 0;
+        ja[0][x] = x;
+    }
+    __syncthreads();
+    int cur = 0;
+    for (uint32_t span = 1; span < 2 * N; span <<= 1) {
+        const int nx = cur ^ 1;
+        for (uint32_t x = tid; x < N; x += nth) {
+            const uint32_t y = jp[cur][x];
+            if (y == NONE) {
+                jp[nx][x] = NONE;
+                jl[nx][x] = jl[cur][x];
+                jm[nx][x] = jm[cur][x];
+                jd[nx][x] = jd[cur][x];
+                ja[nx][x] = ja[cur][x];
+            } else {
+                jp[nx][x] = jp[cur][y];
+                jl[nx][x] = min(jl[cur][x] + jl[cur][y], 2 * N);
+                if (jm[cur][y] < jm[cur][x]) {
+                    jm[nx][x] = jm[cur][y];
+                    jd[nx][x] = jl[cur][x] + jd[cur][y];
+                } else {
+                    jm[nx][x] = jm[cur][x];
+                    jd[nx][x] = jd[cur][x];
+                }
+                ja[nx][x] = ja[cur][y];
+            }
+        }
+        __syncthreads();
+        cur = nx;
+    }
+    uint32_t *P = jp[cur], *Ln = jl[cur], *Mn = jm[cur], *Md = jd[cur], *La = ja[cur];
+    // component (La) and position from its start (Md) of every move source
+    for (uint32_t x = tid; x < N; x += nth) {
+        if (dst_of[x] == NONE) continue;
+        const bool chain = P[x] == NONE;
+        const uint32_t comp = chain ? La[x] : Mn[x];
+        Md[x] = chain ? Ln[x] - 1 : Md[x];
+        La[x] = comp;
+        atomicAdd(&msize[comp], 1u);
+        head[comp] = chain ? 1u : 2u;
+    }
+    __syncthreads();
+    // dense component indices in page order (block scan of the head flags)
+    const uint32_t per = (N + nth - 1) / nth;
+    const uint32_t lo = min(N, tid * per), hi = min(N, (tid + 1) * per);
+    uint32_t cnt = 0;
+    for (uint32_t x = lo; x < hi; ++x) cnt += head[x] ? 1u : 0u;
+    s_scan[tid] = cnt;
+    __syncthreads();
+    for (uint32_t off = 1; off < nth; off <<= 1) {
+        const uint32_t v = tid >= off ? s_scan[tid - off] : 0u;
+        __syncthreads();
+        s_scan[tid] += v;
+        __syncthreads();
+    }
+    uint32_t idx = s_scan[tid] - cnt;
+    for (uint32_t x = lo; x < hi; ++x)
+        if (head[x]) {
+            cinfo[idx] = msize[x] | (head[x] == 2 ? STAGE_BIT : 0u);
+            head[x] = idx;  // page -> dense component index
+            ++idx;
+        }
+    const uint32_t nc = s_scan[nth - 1];
+    __syncthreads();
+    if (nc == 0) return;  // nothing moves
+    uint32_t maxm = 0;
+    for (uint32_t c = tid; c < nc; c += nth) maxm = max(maxm, cinfo[c] & ~STAGE_BIT);
+    for (int o = 16; o; o >>= 1) maxm = max(maxm, __shfl_xor_sync(0xffffffffu, maxm, o));
+    if ((tid & 31) == 0) s_red[tid >> 5] = maxm;
+    __syncthreads();
+    maxm = 0;
+    for (uint32_t i = 0; i < (nth >> 5); ++i) maxm = max(maxm, (uint32_t)s_red[i]);
+    __syncthreads();
+    auto need = [](uint32_t mc, uint32_t L) {
+        const uint32_t m = mc & ~STAGE_BIT, segs = (m + L - 1) / L;
+        return (mc & STAGE_BIT) ? segs : segs - 1;
+    };
+    auto total_need = [&](uint32_t L) -> uint64_t {
+        uint64_t sum = 0;
+        for (uint32_t c = tid; c < nc; c += nth) sum += need(cinfo[c], L);
+        for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if ((tid & 31) == 0) s_red[tid >> 5] = sum;
+        __syncthreads();
+        uint64_t t = 0;
+        for (uint32_t i = 0; i < (nth >> 5); ++i) t += s_red[i];
+        __syncthreads();
+        return t;
+    };
+    // segment length: the smallest L whose total staging fits the pool; if
+    // none does, the smallest with which each component fits a pass alone
+    uint32_t L;
+    if (total_need(maxm) <= a.cap_stage) {
+        uint32_t l0 = 1, h0 = maxm;
+        while (l0 < h0) {
+            const uint32_t mid = (l0 + h0) >> 1;
+            if (total_need(mid) <= a.cap_stage) h0 = mid;
+            else l0 = mid + 1;
+        }
+        L = l0;
+    } else {
+        L = 1;
+        while (L < maxm && need(maxm | STAGE_BIT, L) > a.cap_stage) L = max(L + 1, L * 2);
+        L = min(L, maxm);
+    }
+    // passes: components in order while their staging fits (thread 0; the
+    // number of components of a random page map is small)
+    if (tid == 0) {
+        uint32_t *ws = plan + PLAN_HDR;
+        uint32_t wave = 0, opbase = 0, pass = 0, c = 0, status = 0;
+        while (c < nc) {
+            uint32_t c1 = c, used = 0, nseg = 0, plen = 0;
+            while (c1 < nc) {
+                const uint32_t nd = need(cinfo[c1], L);
+                if (c1 > c && used + nd > a.cap_stage) break;
+                const uint32_t m = cinfo[c1] & ~STAGE_BIT;
+                c_pass[c1] = pass;
+                c_seg[c1] = nseg;
+                c_stg[c1] = used;
+                used += nd;
+                nseg += (m + L - 1) / L;
+                plen = max(plen, min(m, L));
+                ++c1;
+            }
+            const uint64_t pass_ops = used + (uint64_t)plen * nseg;
+            if (used > a.cap_stage || opbase + pass_ops > a.max_ops ||
+                PLAN_HDR + wave + plen + 2 > ops_offset(a.NP)) {
+                status = 2;
+                break;
+            }
+            pass_rec[3 * pass] = opbase;
+            pass_rec[3 * pass + 1] = used;
+            pass_rec[3 * pass + 2] = nseg;
+            ws[wave] = opbase;
+            for (uint32_t w = 1; w <= plen; ++w) ws[wave + w] = opbase + used + (w - 1) * nseg;
+            opbase += (uint32_t)pass_ops;
+            wave += 1 + plen;
+            ws[wave] = opbase;
+            c = c1;
+            ++pass;
+        }
+        misc[0] = L;
+        misc[1] = status;
+        misc[2] = opbase;
+        plan[0] = status ? 0 : wave;
+        plan[1] = opbase;
+        plan[2] = status;
+        plan[3] = pass;
+    }
+    __syncthreads();
+    if (misc[1]) return;
+    L = misc[0];
+    const uint32_t nops = misc[2];
+    uint32_t *ops = plan + ops_offset(a.NP);
+    for (uint32_t o = tid; o < nops; o += nth) {
+        ops[2 * o] = NONE;
+        ops[2 * o + 1] = NONE;
+    }
+    __syncthreads();
+    for (uint32_t x = tid; x < N; x += nth) {
+        if (dst_of[x] == NONE) continue;
+        const uint32_t c = head[La[x]];
+        const uint32_t mc = cinfo[c], m = mc & ~STAGE_BIT;
+        const bool cyc = (mc & STAGE_BIT) != 0;
+        const uint32_t segs = (m + L - 1) / L;
+        const uint32_t k = m - Md[x];
+        const uint32_t sg = (k - 1) / L, w = 1 + (k - 1) % L;
+        const uint32_t pass = c_pass[c];
+        const uint32_t opbase = pass_rec[3 * pass], used = pass_rec[3 * pass + 1],
+                       nseg = pass_rec[3 * pass + 2];
+        const bool st = (k % L == 0 && k < m) || (cyc && k == m);
+        uint32_t src = x;
+        if (st) {
+            const uint32_t sidx = c_stg[c] + ((k == m) ? segs - 1 : k / L - 1);
+            ops[2 * (opbase + sidx)] = x;
+            ops[2 * (opbase + sidx) + 1] = STAGE_BIT | sidx;
+            src = STAGE_BIT | sidx;
+        }
+        const uint32_t slot = opbase + used + (w - 1) * nseg + c_seg[c] + sg;
+        ops[2 * slot] = src;
+        ops[2 * slot + 1] = dst_of[x];
+    }
+}
+
 // One wave: grid.x = ops of the wave, grid.y = chunks of a page. Each block
 // copies one chunk with 16-byte streaming loads and stores.
 __global__ void __launch_bounds__(256) k_rekey_wave(const uint32_t *ops, uint32_t op0,
@@ -189,6 +423,7 @@ __global__ void __launch_bounds__(256) k_rekey_wave(const uint32_t *ops, uint32_
                                                     int64_t page_bytes, int64_t chunk) {
     const uint32_t o = op0 + blockIdx.x;
     const uint32_t s = ops[2 * o], d = ops[2 * o + 1];
+    if (s == NONE) return;  // hole left by a segment shorter than the wave count
     const uint8_t *src = (s & STAGE_BIT) ? stage + (int64_t)(s & ~STAGE_BIT) * page_bytes
                                          : arena + (int64_t)s * page_bytes;
     uint8_t *dst = (d & STAGE_BIT) ? stage + (int64_t)(d & ~STAGE_BIT) * page_bytes
@@ -218,35 +453,53 @@ __global__ void k_copy_words(uint32_t *dst, const uint32_t *src, uint32_t n) {
 cloak_status rekey_run(cloak_ctx *ctx, uint64_t key, uint32_t new_epoch, cudaStream_t s) {
     cloak_status rc;
     if ((rc = keygen_page_map(ctx, key, new_epoch, ctx->d_page_new, s))) return rc;
-    const uint64_t words = rekey_plan_words(ctx->NP);
+    // plan: header + wave table + ops (up to 8 * NPS + 1024 ops) and the
+    // planners' scratch arrays
+    const uint64_t max_ops = 8 * (uint64_t)ctx->NPS + 1024;
+    const uint64_t words = ops_offset(ctx->NP) + 2 * max_ops;
+    const uint64_t scratch = PAR_SCRATCH_ARRAYS * (uint64_t)ctx->NPS + 64;
     if (ctx->plan_cap < words) {
         if (ctx->d_plan) CLOAK_CUDA(ctx, cudaFree(ctx->d_plan));
         ctx->d_plan = nullptr;
-        // plan + 5*NPS+8 scratch words for the planner's arrays
-        CLOAK_CUDA(ctx, cudaMalloc(&ctx->d_plan, (words + 5 * (uint64_t)ctx->NPS + 8) * 4));
+        CLOAK_CUDA(ctx, cudaMalloc(&ctx->d_plan, (words + scratch) * 4));
         ctx->plan_cap = words;
     }
-    PlanArgs pa;
-    pa.old_pa = ctx->d_page_alloc;
-    pa.new_pa = ctx->d_page_new;
-    pa.NP = (uint32_t)ctx->NP;
-    pa.NPS = (uint32_t)ctx->NPS;
-    pa.cap_stage = (uint32_t)ctx->stage_pages;
-    pa.plan = ctx->d_plan;
-    pa.scratch = ctx->d_plan + words;
-    size_t smem = (5 * (size_t)ctx->NPS + 8) * 4;
-    pa.use_smem = smem <= 200 * 1024;
-    if (pa.use_smem) {
-        CLOAK_CUDA(ctx, cudaFuncSetAttribute(k_rekey_plan, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem));
-    } else {
-        smem = 0;
-    }
-    k_rekey_plan<<<1, 1024, smem, s>>>(pa);
+    ParPlan pp;
+    pp.old_pa = ctx->d_page_alloc;
+    pp.new_pa = ctx->d_page_new;
+    pp.NP = (uint32_t)ctx->NP;
+    pp.NPS = (uint32_t)ctx->NPS;
+    pp.cap_stage = (uint32_t)ctx->stage_pages;
+    pp.max_ops = (uint32_t)max_ops;
+    pp.plan = ctx->d_plan;
+    pp.w = ctx->d_plan + words;
+    k_rekey_plan_par<<<1, 1024, 0, s>>>(pp);
     CLOAK_LAUNCHED(ctx);
     uint32_t hdr[PLAN_HDR];
     CLOAK_CUDA(ctx, cudaMemcpyAsync(hdr, ctx->d_plan, sizeof hdr, cudaMemcpyDeviceToHost, s));
     CLOAK_CUDA(ctx, cudaStreamSynchronize(s));
+    if (hdr[2] != 0) {
+        // the compact layout did not fit: the sequential planner packs ops densely
+        PlanArgs pa;
+        pa.old_pa = ctx->d_page_alloc;
+        pa.new_pa = ctx->d_page_new;
+        pa.NP = (uint32_t)ctx->NP;
+        pa.NPS = (uint32_t)ctx->NPS;
+        pa.cap_stage = (uint32_t)ctx->stage_pages;
+        pa.plan = ctx->d_plan;
+        pa.scratch = ctx->d_plan + words;
+        size_t smem = (5 * (size_t)ctx->NPS + 8) * 4;
+        pa.use_smem = smem <= 200 * 1024;
+        if (pa.use_smem)
+            CLOAK_CUDA(ctx, cudaFuncSetAttribute(k_rekey_plan,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        else
+            smem = 0;
+        k_rekey_plan<<<1, 1024, smem, s>>>(pa);
+        CLOAK_LAUNCHED(ctx);
+        CLOAK_CUDA(ctx, cudaMemcpyAsync(hdr, ctx->d_plan, sizeof hdr, cudaMemcpyDeviceToHost, s));
+        CLOAK_CUDA(ctx, cudaStreamSynchronize(s));
+    }
     if (hdr[2] != 0) {
         ctx->last_err = "re-key plan does not fit the staging pool";
         return CLOAK_E_UNSUPPORTED;
