@@ -169,11 +169,11 @@ struct TcCfg {
     static constexpr int A_BYTES = FP8 ? 16384 : 32768;
     static constexpr int B_BYTES = NPAD * (FP8 ? 128 : 256);
     static constexpr int STAGE = A_BYTES + B_BYTES;
-    static constexpr int STAGES = std::min(8, (200 * 1024) / STAGE);
+    static constexpr int STAGES = std::min(16, (220 * 1024) / STAGE);
     static constexpr int KSTEPS = FP8 ? 4 : 8;  // MMAs per 128-wide tile
     static constexpr int TMEM_COLS = (2 * NPAD <= 32) ? 32 : (2 * NPAD <= 64) ? 64
                                    : (2 * NPAD <= 128) ? 128 : (2 * NPAD <= 256) ? 256 : 512;
-    static constexpr int SMEM = STAGES * STAGE + 1024 + 256;
+    static constexpr int SMEM = STAGES * STAGE + 1024 + 512;  // align + barriers
     static constexpr uint32_t IDESC = idesc_make(FP8 ? 0u : 1u, 128, NPAD);
 };
 
