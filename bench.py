@@ -291,21 +291,44 @@ def bench_extras(cloak, synth, torch, dev, stream, key, steps):
     cm.close()
     torch.cuda.empty_cache()
 
-    # re-key of the whole 32-layer BF16 stack (12.95 GB, 6,176 pages + 64 spare).
-    # The arena holds random bytes: a page copy costs the same whatever it holds.
+    # the 32-layer BF16 stack (12.95 GB): one persistent launch per decode
+    # step (all 224 cloaked linears + glue, grid barriers between dependent
+    # stages), replayed from a CUDA graph; then the in-place re-key of it.
     model = synth.llama7b_layer(32)
-    cm = cloak.CloakModel(model, device=dev, twin=False)
+    cm = cloak.CloakModel(model, device=dev, twin=True)
     t0 = time.perf_counter()
     cm.keygen(key, 0)
     kg_ms = (time.perf_counter() - t0) * 1e3
-    arena = cm.arena_bytes(0)
-    g = torch.Generator(device=f"cuda:{dev}")
-    g.manual_seed(11)
-    for off in range(0, arena.numel(), 1 << 30):
-        seg = arena[off:off + (1 << 30)]
-        seg.copy_(torch.randint(0, 256, seg.shape, dtype=torch.uint8, device=seg.device, generator=g))
-    del arena
+    for t in range(len(model.tensors)):
+        w = synth.weights_device(model, t, seed=0)
+        cm.shuffle(t, w)
+        del w
     torch.cuda.synchronize()
+    desc = cm.stack_desc()
+    wbytes = sum(t.n * t.k * 2 for t in model.tensors)
+    stk = {}
+    for M in (1, 8, 32, 64):
+        h0 = torch.from_numpy(synth.activations_host(M, 4096, seed=M)).cuda()
+        res = {}
+        for name, unc in (("cloaked", False), ("uncloaked", True)):
+            hb = h0.clone()
+            def fn(hb=hb, unc=unc):
+                hb.copy_(h0)
+                cm.stack_decode(hb, uncloaked=unc, desc=desc, stream=stream.cuda_stream)
+            try:
+                g2 = graph(fn)
+                res[name] = timed(g2.replay, 10)
+                del g2
+            except Exception as e:  # graph capture refused: time eager launches
+                res[name] = timed(fn, 10)
+                res["graph_error"] = str(e)[:120]
+        bytes_step = wbytes + 4 * cm.G + 32 * 2 * M * (4096 * 4 + 11008 * 2) * 2
+        stk[str(M)] = {"cloaked_ms": round(res["cloaked"], 4), "uncloaked_ms": round(res["uncloaked"], 4),
+                       "cloaked_gbs": round(bytes_step / (res["cloaked"] / 1e3) / 1e9, 1),
+                       "uncloaked_gbs": round(bytes_step / (res["uncloaked"] / 1e3) / 1e9, 1),
+                       "tokens_per_s": round(M / (res["cloaked"] / 1e3), 1)}
+    assert cm.device_status() == 0
+    out["stack_decode_llama7b_32L"] = stk
     ts = []
     for e in range(1, 5):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -212,6 +212,29 @@ CLOAK_API cloak_status cloak_linear_noalloc(cloak_ctx *ctx, int32_t tensor, cons
                                             void *y_dev, int32_t M, int32_t out_dtype,
                                             int32_t flags, void *stream);
 
+/* A LLaMA-style decoder stack whose seven linears per layer are cloaked
+ * tensors of this context (BF16, head_dim 128). */
+typedef struct {
+    int32_t num_layers;
+    const int32_t *layer_tensors;  /* [num_layers * 7]: q, k, v, o, gate, up, down */
+    int32_t d_model, n_heads, n_kv_heads, head_dim, d_ff;
+    float rms_eps;
+} cloak_stack_desc;
+
+/* One decode step of the whole stack in a single persistent launch (all
+ * layers' cloaked linears plus the glue, grid barriers between dependent
+ * stages; CUDA-graph capturable after a first call has sized the workspace).
+ * h_dev is the FP32 residual stream [M, d_model], updated in place. Per
+ * layer, with r = 1/sqrt(mean(h^2) + eps) per token and unit norm gains:
+ * q,k,v = (h W^T) r; the attention of a single token is its own value, each
+ * query head taking its group's v; h += a Wo^T; g,u = (h W^T) r';
+ * h += (silu(g) * u) Wd^T. Intra-layer permutations cancel inside the layer
+ * (the stored head order is consistent across q, k, v, o and the MLP order
+ * across gate, up, down). 1 <= M <= 64. flags: CLOAK_LINEAR_UNCLOAKED runs on
+ * the twin. Device waits are bounded; a timeout sets cloak_device_status. */
+CLOAK_API cloak_status cloak_stack_decode(cloak_ctx *ctx, const cloak_stack_desc *desc, float *h_dev,
+                                          int32_t M, int32_t flags, void *stream);
+
 /* Re-key (periodic re-randomisation, Section 4.2 and Figure 7): draw the page
  * map of (key, new_epoch) and move every placed page to its new physical page
  * in place, through a small staging pool, so the arena ends bit-identical to

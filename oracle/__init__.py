@@ -344,3 +344,34 @@ def contiguity(page_alloc: np.ndarray, NP: int) -> float:
     if NP < 2:
         return 1.0
     return float(np.mean(pm[1:] == pm[:-1] + 1))
+
+
+# ------------------------------------------------------------- layer stack
+
+def silu(g):
+    return g / (1.0 + np.exp(-g))
+
+
+def stack_decode_f64(model, W64, h0, eps=1e-5):
+    """One decode step of a LLaMA-style decoder stack in FP64 (the reference
+    of the persistent stack launch). W64: per tensor, the weights as FP64 in
+    descriptor order (q, k, v, o, gate, up, down per layer). Per layer, with
+    r = 1/sqrt(mean(h^2) + eps) per token and unit norm gains:
+      v = (h r) Wv^T; a = the value of the single token itself (softmax over
+      one score is 1), query head j reading KV head j // (H / H_kv);
+      h += a Wo^T; g, u = (h r') W^T; h += (silu(g) * u) Wd^T.
+    q and k do not affect a one-token step."""
+    h = np.asarray(h0, np.float64).copy()
+    M = h.shape[0]
+    H, Hkv, hd = model.n_heads, model.n_kv_heads, model.head_dim
+    for l in range(model.num_layers):
+        ts = {t.kind: i for i, t in enumerate(model.tensors) if t.layer == l}
+        r = 1.0 / np.sqrt(np.mean(h * h, axis=1, keepdims=True) + eps)
+        v = linear_f64(h * r, W64[ts[4]])                         # kind 4 = v
+        a = np.repeat(v.reshape(M, Hkv, hd), H // Hkv, axis=1).reshape(M, H * hd)
+        h = h + linear_f64(a, W64[ts[5]])                         # o
+        r = 1.0 / np.sqrt(np.mean(h * h, axis=1, keepdims=True) + eps)
+        g = linear_f64(h * r, W64[ts[6]])                         # gate
+        u = linear_f64(h * r, W64[ts[7]])                         # up
+        h = h + linear_f64(silu(g) * u, W64[ts[8]])               # down
+    return h

@@ -49,6 +49,12 @@ class ModelDesc(C.Structure):
                 ("page_bytes", C.c_int64)]
 
 
+class StackDesc(C.Structure):
+    _fields_ = [("num_layers", C.c_int32), ("layer_tensors", C.POINTER(C.c_int32)),
+                ("d_model", C.c_int32), ("n_heads", C.c_int32), ("n_kv_heads", C.c_int32),
+                ("head_dim", C.c_int32), ("d_ff", C.c_int32), ("rms_eps", C.c_float)]
+
+
 # (name, restype, argtypes); the list is the ABI this binding expects
 _vp, _i32, _i64, _u32, _u64 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint32, C.c_uint64
 SIGNATURES = [
@@ -66,6 +72,7 @@ SIGNATURES = [
                                   _i32, _i32, _vp]),
     ("cloak_linear_host", _i32, [_vp, _i32, _vp, _vp, _i32, _i32, _i32, _vp]),
     ("cloak_linear_noalloc", _i32, [_vp, _i32, _vp, _vp, _i32, _i32, _i32, _vp]),
+    ("cloak_stack_decode", _i32, [_vp, C.POINTER(StackDesc), _vp, _i32, _i32, _vp]),
     ("cloak_rekey", _i32, [_vp, _u64, _u32, _vp]),
     ("cloak_device_status", _i32, [_vp]),
     ("cloak_last_error", C.c_char_p, [_vp]),
@@ -185,6 +192,11 @@ def cloak_linear_noalloc(ctx, tensor: int, x_dev: int, y_dev: int, M: int, out_d
                          flags: int = 0, stream=None):
     _check("cloak_linear_noalloc", load().cloak_linear_noalloc(ctx, tensor, x_dev, y_dev, M, out_dtype,
                                                                flags, _stream(stream)), ctx)
+
+
+def cloak_stack_decode(ctx, desc: StackDesc, h_dev: int, M: int, flags: int = 0, stream=None):
+    _check("cloak_stack_decode", load().cloak_stack_decode(ctx, C.byref(desc), h_dev, M, flags,
+                                                           _stream(stream)), ctx)
 
 
 def cloak_rekey(ctx, key: int, new_epoch: int, stream=None):
@@ -308,6 +320,28 @@ class CloakModel:
         cloak_linear_batch(self.ctx, list(tensors), [x.data_ptr() for x in xs],
                            [y.data_ptr() for y in ys], M, out_dtype, flags, stream)
         return ys
+
+    def stack_desc(self, eps=1e-5):
+        """Descriptor of the decoder stack of this model (tensor kinds q, k,
+        v, o, gate, up, down per layer)."""
+        m = self.model
+        order = []
+        for l in range(m.num_layers):
+            ts = {t.kind: i for i, t in enumerate(m.tensors) if t.layer == l}
+            order += [ts[k] for k in (synth.K_Q, synth.K_K, synth.K_V, synth.K_O, synth.K_GATE,
+                                      synth.K_UP, synth.K_DOWN)]
+        self._stack_tensors = (C.c_int32 * len(order))(*order)
+        return StackDesc(m.num_layers, self._stack_tensors, m.d_model, m.n_heads, m.n_kv_heads,
+                         m.head_dim, m.d_ff, eps)
+
+    def stack_decode(self, h, uncloaked=False, desc=None, stream=None):
+        """One decode step of the whole stack; h: FP32 [M, d_model], in place."""
+        import torch
+        assert h.dtype == torch.float32 and h.is_cuda and h.is_contiguous()
+        d = desc or self.stack_desc()
+        cloak_stack_decode(self.ctx, d, h.data_ptr(), h.shape[0],
+                           LINEAR_UNCLOAKED if uncloaked else 0, stream)
+        return h
 
     def rekey(self, key, new_epoch, stream=None):
         cloak_rekey(self.ctx, key, new_epoch, stream)

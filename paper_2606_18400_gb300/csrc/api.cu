@@ -141,6 +141,7 @@ static void release(cloak_ctx *c) {
     F(c->d_page_alloc); F(c->d_tile_slot); F(c->d_page_new); F(c->d_tile_inv); F(c->d_info);
     F(c->arena); F(c->twin); F(c->d_scales); F(c->d_part); F(c->d_rowcnt); F(c->d_xq);
     F(c->d_xs); F(c->d_xstage); F(c->d_ystage); F(c->d_stage); F(c->d_plan); F(c->d_status);
+    F(c->d_stack_ws);
     KeygenWork &w = c->kw;
     uint32_t *arrs[] = {w.j, w.first, w.cnt, w.boff, w.cursor, w.bucket, w.succ, w.ptr0,
                         w.ptr1, w.val0, w.val1, w.out, w.counters, w.seg_off};
@@ -375,6 +376,15 @@ extern "C" cloak_status cloak_linear_host(cloak_ctx *ctx, int32_t tensor, const 
     CLOAK_CUDA(ctx, cudaMemcpyAsync(y_host, ctx->d_ystage, yb, cudaMemcpyDeviceToHost, s));
     CLOAK_CUDA(ctx, cudaStreamSynchronize(s));
     return CLOAK_OK;
+}
+
+extern "C" cloak_status cloak_stack_decode(cloak_ctx *ctx, const cloak_stack_desc *desc, float *h_dev,
+                                           int32_t M, int32_t flags, void *stream) {
+    if (!ctx || !desc || !desc->layer_tensors || !h_dev || ((uintptr_t)h_dev & 15) || (flags & ~1))
+        return CLOAK_E_INVAL;
+    if (!ctx->keyed) return CLOAK_E_STATE;
+    CLOAK_CUDA(ctx, cudaSetDevice(ctx->device));
+    return stack_decode_run(ctx, desc, h_dev, M, flags, (cudaStream_t)stream);
 }
 
 extern "C" cloak_status cloak_rekey(cloak_ctx *ctx, uint64_t key, uint32_t new_epoch, void *stream) {

@@ -87,6 +87,9 @@ struct cloak_ctx {
     uint32_t *d_plan = nullptr;                // re-key move plan
     size_t plan_cap = 0;
     int *d_status = nullptr;
+    void *d_stack_ws = nullptr;                // layer-stack decode workspace
+    size_t stack_ws_cap = 0;
+    std::vector<uint8_t> stack_sig;            // stage program last uploaded
 
     bool keyed = false, placed_any = false;
     uint64_t key = 0;
@@ -134,6 +137,8 @@ cloak_status linear_run(cloak_ctx *ctx, int t, const void *x, void *y, int M, in
                         int flags, cudaStream_t s);
 cloak_status linear_batch_run(cloak_ctx *ctx, int n, const int32_t *tensors, const void *const *xs,
                               void *const *ys, int M, int out_dtype, int flags, cudaStream_t s);
+cloak_status stack_decode_run(cloak_ctx *ctx, const cloak_stack_desc *d, float *h, int M, int flags,
+                              cudaStream_t s);
 cloak_status linear_run_given_scratch(cloak_ctx *ctx, int t, const void *x, void *y, int M,
                                       int out_dtype, int flags, float *part, size_t part_floats,
                                       uint32_t *rowcnt, uint32_t max_grid, cudaStream_t s);

@@ -31,7 +31,6 @@
 
 namespace cloak {
 
-__device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
 
 // ------------------------------------------------------------ FP32 (SIMT)
 
@@ -177,9 +176,6 @@ struct TcCfg {
     static constexpr uint32_t IDESC = idesc_make(FP8 ? 0u : 1u, 128, NPAD);
 };
 
-__device__ __forceinline__ uint32_t cta_of_unit(uint64_t u, uint64_t G, uint64_t T) {
-    return (uint32_t)(((u + 1) * G - 1) / T);
-}
 
 // position of a unit: problem, tile row, tile column, first unit of its row
 struct Loc {

@@ -26,6 +26,14 @@ CLOAK_DEV unsigned long long globaltimer() {
 
 CLOAK_DEV uint32_t elect_lane0() { return (threadIdx.x & 31) == 0; }
 
+CLOAK_DEV uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
+
+// CTA that owns unit u when T units are split evenly over G CTAs
+// (CTA c owns [c*T/G, (c+1)*T/G))
+CLOAK_DEV uint32_t cta_of_unit(uint64_t u, uint64_t G, uint64_t T) {
+    return (uint32_t)(((u + 1) * G - 1) / T);
+}
+
 // ------------------------------------------------------------------ mbarrier
 CLOAK_DEV void mbar_init(uint64_t *bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));

@@ -349,3 +349,64 @@ def test_stored_codes_are_the_placed_tiles(mi):
                                   O.tile_of(om, codes, u // kt, u % kt))
         if sc is not None:
             assert np.array_equal(sc, scales[t])
+
+
+def _stack_model(layers=2, dtype=synth.DT_F32):
+    m = synth.small_decoder(layers, dtype, d_model=256, n_heads=4, n_kv_heads=2, d_ff=192,
+                            head_dim=64, spare_pages=1)
+    m.tile_r = m.tile_c = 64
+    m.page_bytes = 4 * 64 * 64 * 4
+    return m
+
+
+def test_stack_reference_is_invariant_under_the_keyed_permutations():
+    """The stack reference on the stored (permuted) weights equals it on the
+    logical weights (FP64, up to summation order), for several keys: the GQA
+    head grouping (query head j reads KV head j // ratio) is exactly what the
+    keyed head permutation preserves."""
+    m = _stack_model()
+    om = O.OracleModel(m)
+    Ws = synth.weights_host(m, seed=11, std=0.1)
+    h0 = np.random.default_rng(3).standard_normal((3, 256))
+    ref = O.stack_decode_f64(m, [w.astype(np.float64) for w in Ws], h0)
+    for key in range(4):
+        tb = O.keygen(om, key, 0)
+        arena, _ = O.shuffle_model(om, tb, Ws)
+        S = [O.stored_f64(om, tb, t, arena) for t in range(len(Ws))]
+        assert np.max(np.abs(O.stack_decode_f64(m, S, h0) - ref)) < 1e-10
+
+
+def test_stack_reference_one_token_attention_is_softmax_attention():
+    """With a single token the attention output equals full softmax attention
+    over a sequence of length one."""
+    m = _stack_model(1)
+    Ws = [w.astype(np.float64) for w in synth.weights_host(m, seed=12, std=0.1)]
+    x = np.random.default_rng(4).standard_normal((1, 256))
+    Wq, Wk, Wv, Wo = Ws[0], Ws[1], Ws[2], Ws[3]
+    full = _attention_block(x, Wq, Wk, Wv, Wo, 4, 2, 64, 1)
+    r = 1.0 / np.sqrt(np.mean(x * x) + 1e-5)
+    # the oracle's attention term of the first layer, isolated
+    v = (x * r) @ Wv.T
+    a = np.repeat(v.reshape(1, 2, 64), 2, axis=1).reshape(1, 256)
+    assert np.allclose(a @ Wo.T, _attention_block(x * r, Wq, Wk, Wv, Wo, 4, 2, 64, 1), atol=1e-12)
+    assert full.shape == (1, 256)
+
+
+def test_stack_reference_single_layer_by_hand():
+    """Brute-force loops for one token through one layer."""
+    m = _stack_model(1)
+    Ws = [w.astype(np.float64) for w in synth.weights_host(m, seed=13, std=0.1)]
+    h = np.random.default_rng(5).standard_normal((1, 256))
+    got = O.stack_decode_f64(m, Ws, h)[0]
+    D, F = 256, 192
+    hh = list(h[0])
+    r = 1.0 / np.sqrt(sum(z * z for z in hh) / D + 1e-5)
+    v = [sum(hh[k] * r * Ws[2][n, k] for k in range(D)) for n in range(128)]
+    a = [v[(j // 2) * 64 + d] for j in range(4) for d in range(64)]
+    hh = [hh[n] + sum(a[k] * Ws[3][n, k] for k in range(256)) for n in range(D)]
+    r = 1.0 / np.sqrt(sum(z * z for z in hh) / D + 1e-5)
+    g = [sum(hh[k] * r * Ws[4][n, k] for k in range(D)) for n in range(F)]
+    u = [sum(hh[k] * r * Ws[5][n, k] for k in range(D)) for n in range(F)]
+    act = [g[i] / (1 + np.exp(-g[i])) * u[i] for i in range(F)]
+    hh = [hh[n] + sum(act[k] * Ws[6][n, k] for k in range(F)) for n in range(D)]
+    assert np.allclose(got, hh, rtol=0, atol=1e-9)
