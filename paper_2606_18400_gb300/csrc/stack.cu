@@ -431,10 +431,15 @@ __global__ void __launch_bounds__(192, 1)
                     asm volatile("bar.sync 1, 128;" ::: "memory");
                     const uint32_t c_first = cta_of_unit(rs, G, T), c_last = cta_of_unit(re - 1, G, T);
                     if (et == 0) {
+                        // CTAs in [c_first, c_last] with an empty range (a stage
+                        // with fewer units than CTAs) hold no piece of the row
+                        uint32_t pieces = 0;
+                        for (uint32_t c = c_first; c <= c_last; ++c)
+                            pieces += ((uint64_t)c * T / G < ((uint64_t)c + 1) * T / G) ? 1u : 0u;
                         __threadfence();
                         const uint32_t old = atomicAdd(P.rowcnt + l.nt, 1u);
                         __threadfence();
-                        *last_flag = (old == c_last - c_first) ? 1u : 0u;
+                        *last_flag = (old == pieces - 1) ? 1u : 0u;
                     }
                     asm volatile("bar.sync 1, 128;" ::: "memory");
                     if (*last_flag) {
@@ -444,6 +449,7 @@ __global__ void __launch_bounds__(192, 1)
 #pragma unroll
                             for (int j = 0; j < 16; ++j) ag[j] = au[j] = 0.0f;
                             for (uint32_t c = c_first; c <= c_last; ++c) {
+                                if ((uint64_t)c * T / G >= ((uint64_t)c + 1) * T / G) continue;
                                 const SLoc lc = sloc(st, (uint64_t)c * T / G);
                                 const int ps = (lc.p == l.p && lc.nt == l.nt) ? 0 : 1;
                                 const float *pp = a.part + ((((uint64_t)c * 2 + ps) * 2) * 128 + r_in) * NPAD + c0;
@@ -562,8 +568,11 @@ cloak_status stack_decode_run(cloak_ctx *ctx, const cloak_stack_desc *d, float *
     size_t rows = 0;
     for (int l = 0; l < d->num_layers; ++l)
         for (int j = 0; j < 7; ++j) rows += ctx->info[d->layer_tensors[l * 7 + j]].nt;
-    const size_t bytes = act_elems * 2 + 256 + part_floats * 4 + 256 + rows * 4 + 256 +
-                         nstages * sizeof(StackStage) + 256;
+    auto r256 = [](size_t n) { return (n + 255) & ~(size_t)255; };
+    const size_t bytes = r256((size_t)M * D * 2) + r256((size_t)M * HQ * 2) + 2 * r256((size_t)M * HKV * 2) +
+                         r256((size_t)M * F * 2) + r256(part_floats * 4) + r256(rows * 4) + r256(8) +
+                         r256(nstages * sizeof(StackStage));
+    (void)act_elems;
     cudaError_t err = cudaSuccess;
     void *before = ctx->d_stack_ws;
     uint8_t *w = (uint8_t *)grow(ctx, ctx->d_stack_ws, ctx->stack_ws_cap, bytes, err);
