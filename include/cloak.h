@@ -235,6 +235,45 @@ typedef struct {
 CLOAK_API cloak_status cloak_stack_decode(cloak_ctx *ctx, const cloak_stack_desc *desc, float *h_dev,
                                           int32_t M, int32_t flags, void *stream);
 
+/* A served model: the decoder stack, a cloaked lm_head tensor [vocab,
+ * d_model], a plain BF16 embedding table [vocab, d_model] (device, caller's)
+ * and the paged KV cache (device, caller's): per layer, num_blocks blocks of
+ * 16 tokens x n_kv_heads x 128, BF16, for keys and for values. */
+typedef struct {
+    cloak_stack_desc stack;
+    int32_t lm_head;          /* tensor index of the output projection        */
+    int32_t vocab;
+    const void *embedding;    /* BF16 [vocab, d_model]                          */
+    void *k_cache, *v_cache;  /* BF16 [layers][num_blocks][16][n_kv][128]       */
+    int32_t num_blocks;
+    int32_t max_blocks;       /* block-table row length (blocks per request)    */
+    float rope_theta;
+} cloak_serve_desc;
+
+/* One step's batch: num_tokens tokens of any requests (prefill chunks and
+ * decode tokens mixed). All arrays are device int32. Token m of request
+ * req_slots[m] sits at position positions[m] and attends to that request's
+ * positions 0..positions[m] through block_tables[req][pos / 16] (a request's
+ * earlier positions must be in the cache or in this batch). sample_rows lists
+ * the tokens whose next token is sampled (greedy) into out_tokens;
+ * out_logits (FP32 [num_sample, vocab], may be NULL) receives their logits. */
+typedef struct {
+    int32_t num_tokens, num_sample, flags;  /* flags: CLOAK_LINEAR_UNCLOAKED   */
+    const int32_t *token_ids, *positions, *req_slots, *block_tables, *sample_rows;
+    int32_t *out_tokens;
+    float *out_logits;
+} cloak_serve_batch;
+
+/* One forward step of the served model over a mixed batch: per layer
+ * RMSNorm, cloaked q/k/v, RoPE (theta, rotate-half pairs), KV-cache write,
+ * causal paged attention (GQA), cloaked o + residual, RMSNorm, cloaked
+ * gate/up, SiLU-gated product, cloaked down + residual; then RMSNorm, the
+ * cloaked lm_head at the sampled rows and greedy argmax. Enqueued on `stream`;
+ * the context-owned workspace grows with the batch. A token's results depend
+ * only on its own request, so a request computes the same alone or batched. */
+CLOAK_API cloak_status cloak_serve_step(cloak_ctx *ctx, const cloak_serve_desc *desc,
+                                        const cloak_serve_batch *batch, void *stream);
+
 /* Re-key (periodic re-randomisation, Section 4.2 and Figure 7): draw the page
  * map of (key, new_epoch) and move every placed page to its new physical page
  * in place, through a small staging pool, so the arena ends bit-identical to

@@ -375,3 +375,46 @@ def stack_decode_f64(model, W64, h0, eps=1e-5):
         u = linear_f64(h * r, W64[ts[7]])                         # up
         h = h + linear_f64(silu(g) * u, W64[ts[8]])               # down
     return h
+
+
+# ------------------------------------------------------------- full forward
+
+def rope_f64(x, pos, theta=10000.0):
+    """Rotary embedding of 128-dim heads: pairs (i, i+64) rotated by
+    pos * theta^(-i/64). x: [T, heads, 128], pos: [T]."""
+    i = np.arange(64, dtype=np.float64)
+    ang = np.asarray(pos, np.float64)[:, None] * theta ** (-i / 64.0)
+    c, s = np.cos(ang)[:, None, :], np.sin(ang)[:, None, :]
+    a, b = x[..., :64], x[..., 64:]
+    return np.concatenate([a * c - b * s, b * c + a * s], axis=-1)
+
+
+def transformer_logits_f64(model, W64, emb64, tokens, eps=1e-5, theta=10000.0):
+    """Logits of every position of one sequence through the full model in
+    FP64 (the reference of the serving step): embedding, per layer RMSNorm
+    (unit gain), q/k/v, RoPE, causal softmax attention (GQA: query head j uses
+    KV head j // (H/H_kv)), o + residual, RMSNorm, SwiGLU MLP + residual; final
+    RMSNorm and the output projection."""
+    T = len(tokens)
+    H, Hkv, hd = model.n_heads, model.n_kv_heads, 128
+    h = np.asarray(emb64, np.float64)[np.asarray(tokens)]
+    pos = np.arange(T)
+    ts_lm = [i for i, t in enumerate(model.tensors) if t.kind == 9][0]
+    norm = lambda z: z / np.sqrt(np.mean(z * z, axis=1, keepdims=True) + eps)
+    for l in range(model.tensors[ts_lm].layer):
+        ts = {t.kind: i for i, t in enumerate(model.tensors) if t.layer == l}
+        x = norm(h)
+        q = rope_f64((x @ W64[ts[2]].T).reshape(T, H, hd), pos, theta)
+        k = rope_f64((x @ W64[ts[3]].T).reshape(T, Hkv, hd), pos, theta)
+        v = (x @ W64[ts[4]].T).reshape(T, Hkv, hd)
+        a = np.zeros((T, H, hd))
+        for j in range(H):
+            kv = j // (H // Hkv)
+            sc = q[:, j] @ k[:, kv].T / np.sqrt(hd) + np.triu(np.full((T, T), -np.inf), 1)
+            p = np.exp(sc - sc.max(1, keepdims=True))
+            a[:, j] = (p / p.sum(1, keepdims=True)) @ v[:, kv]
+        h = h + a.reshape(T, H * hd) @ W64[ts[5]].T
+        x = norm(h)
+        g, u = x @ W64[ts[6]].T, x @ W64[ts[7]].T
+        h = h + (silu(g) * u) @ W64[ts[8]].T
+    return norm(h) @ W64[ts_lm].T

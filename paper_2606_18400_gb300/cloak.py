@@ -55,6 +55,19 @@ class StackDesc(C.Structure):
                 ("head_dim", C.c_int32), ("d_ff", C.c_int32), ("rms_eps", C.c_float)]
 
 
+class ServeDesc(C.Structure):
+    _fields_ = [("stack", StackDesc), ("lm_head", C.c_int32), ("vocab", C.c_int32),
+                ("embedding", C.c_void_p), ("k_cache", C.c_void_p), ("v_cache", C.c_void_p),
+                ("num_blocks", C.c_int32), ("max_blocks", C.c_int32), ("rope_theta", C.c_float)]
+
+
+class ServeBatch(C.Structure):
+    _fields_ = [("num_tokens", C.c_int32), ("num_sample", C.c_int32), ("flags", C.c_int32),
+                ("token_ids", C.c_void_p), ("positions", C.c_void_p), ("req_slots", C.c_void_p),
+                ("block_tables", C.c_void_p), ("sample_rows", C.c_void_p),
+                ("out_tokens", C.c_void_p), ("out_logits", C.c_void_p)]
+
+
 # (name, restype, argtypes); the list is the ABI this binding expects
 _vp, _i32, _i64, _u32, _u64 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint32, C.c_uint64
 SIGNATURES = [
@@ -73,6 +86,7 @@ SIGNATURES = [
     ("cloak_linear_host", _i32, [_vp, _i32, _vp, _vp, _i32, _i32, _i32, _vp]),
     ("cloak_linear_noalloc", _i32, [_vp, _i32, _vp, _vp, _i32, _i32, _i32, _vp]),
     ("cloak_stack_decode", _i32, [_vp, C.POINTER(StackDesc), _vp, _i32, _i32, _vp]),
+    ("cloak_serve_step", _i32, [_vp, C.POINTER(ServeDesc), C.POINTER(ServeBatch), _vp]),
     ("cloak_rekey", _i32, [_vp, _u64, _u32, _vp]),
     ("cloak_device_status", _i32, [_vp]),
     ("cloak_last_error", C.c_char_p, [_vp]),
@@ -197,6 +211,11 @@ def cloak_linear_noalloc(ctx, tensor: int, x_dev: int, y_dev: int, M: int, out_d
 def cloak_stack_decode(ctx, desc: StackDesc, h_dev: int, M: int, flags: int = 0, stream=None):
     _check("cloak_stack_decode", load().cloak_stack_decode(ctx, C.byref(desc), h_dev, M, flags,
                                                            _stream(stream)), ctx)
+
+
+def cloak_serve_step(ctx, desc: ServeDesc, batch: ServeBatch, stream=None):
+    _check("cloak_serve_step", load().cloak_serve_step(ctx, C.byref(desc), C.byref(batch),
+                                                       _stream(stream)), ctx)
 
 
 def cloak_rekey(ctx, key: int, new_epoch: int, stream=None):
@@ -326,12 +345,13 @@ class CloakModel:
         v, o, gate, up, down per layer)."""
         m = self.model
         order = []
-        for l in range(m.num_layers):
+        layers = sorted({t.layer for t in m.tensors if t.kind == synth.K_Q})
+        for l in layers:
             ts = {t.kind: i for i, t in enumerate(m.tensors) if t.layer == l}
             order += [ts[k] for k in (synth.K_Q, synth.K_K, synth.K_V, synth.K_O, synth.K_GATE,
                                       synth.K_UP, synth.K_DOWN)]
         self._stack_tensors = (C.c_int32 * len(order))(*order)
-        return StackDesc(m.num_layers, self._stack_tensors, m.d_model, m.n_heads, m.n_kv_heads,
+        return StackDesc(len(layers), self._stack_tensors, m.d_model, m.n_heads, m.n_kv_heads,
                          m.head_dim, m.d_ff, eps)
 
     def stack_decode(self, h, uncloaked=False, desc=None, stream=None):

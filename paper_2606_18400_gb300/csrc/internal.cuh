@@ -90,6 +90,8 @@ struct cloak_ctx {
     void *d_stack_ws = nullptr;                // layer-stack decode workspace
     size_t stack_ws_cap = 0;
     std::vector<uint8_t> stack_sig;            // stage program last uploaded
+    void *d_serve_ws = nullptr;                // serving-step workspace
+    size_t serve_ws_cap = 0;
 
     bool keyed = false, placed_any = false;
     uint64_t key = 0;
@@ -137,6 +139,8 @@ cloak_status linear_run(cloak_ctx *ctx, int t, const void *x, void *y, int M, in
                         int flags, cudaStream_t s);
 cloak_status linear_batch_run(cloak_ctx *ctx, int n, const int32_t *tensors, const void *const *xs,
                               void *const *ys, int M, int out_dtype, int flags, cudaStream_t s);
+cloak_status serve_step_run(cloak_ctx *ctx, const cloak_serve_desc *d, const cloak_serve_batch *b,
+                            cudaStream_t s);
 cloak_status stack_decode_run(cloak_ctx *ctx, const cloak_stack_desc *d, float *h, int M, int flags,
                               cudaStream_t s);
 cloak_status linear_run_given_scratch(cloak_ctx *ctx, int t, const void *x, void *y, int M,

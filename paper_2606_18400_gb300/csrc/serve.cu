@@ -1,0 +1,272 @@
+// serve.cu -- one forward step of a continuously batched LLaMA-style model
+// over the cloaked arena: a mixed batch of prefill-chunk and decode tokens of
+// many requests, with a paged KV cache (the serving loop of the host decides
+// the batch; this file runs it on the device).
+//
+// Per layer, tokens independent except through their own request's KV cache:
+//   x = rmsnorm(h); q, k, v = cloaked linears of x; RoPE(q, k); k, v -> cache;
+//   a = causal attention of q over its request's cached keys/values (GQA);
+//   h += cloaked o(a); x = rmsnorm(h); g, u = cloaked gate/up of x;
+//   h += cloaked down(silu(g) * u)
+// then logits = cloaked lm_head(rmsnorm(h)) at the sampled rows, greedy argmax.
+// Every token's result depends only on its own inputs and its request's cache
+// (the linears' split does not depend on the batch size), so a request gets
+// the same numbers alone and in a mix.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cfloat>
+#include <cmath>
+
+#include "internal.cuh"
+
+namespace cloak {
+
+static inline unsigned nb(size_t n, unsigned b = 256) { return (unsigned)((n + b - 1) / b); }
+
+__global__ void k_embed(const __nv_bfloat16 *emb, const int32_t *ids, int D, float *h) {
+    const int m = blockIdx.x;
+    const __nv_bfloat16 *e = emb + (size_t)ids[m] * D;
+    for (int c = threadIdx.x; c < D; c += blockDim.x) h[(size_t)m * D + c] = __bfloat162float(e[c]);
+}
+
+// x = bf16(h * r), r = 1/sqrt(mean(h^2) + eps); optional row subset
+__global__ void k_rmsnorm(const float *h, const int32_t *rows, int D, float eps, __nv_bfloat16 *x) {
+    const int m = blockIdx.x;
+    const int src = rows ? rows[m] : m;
+    const float *hr = h + (size_t)src * D;
+    float ss = 0.0f;
+    for (int c = threadIdx.x; c < D; c += blockDim.x) ss += hr[c] * hr[c];
+    __shared__ float red[32];
+    for (int o = 16; o; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ss;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        ss = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0f;
+        for (int o = 16; o; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        if (threadIdx.x == 0) red[0] = rsqrtf(ss / (float)D + eps);
+    }
+    __syncthreads();
+    const float r = red[0];
+    for (int c = threadIdx.x; c < D; c += blockDim.x) x[(size_t)m * D + c] = __float2bfloat16_rn(hr[c] * r);
+}
+
+// RoPE (rotate-half pairs (i, i+64) of a 128-dim head, angle pos * theta^(-i/64))
+// on q and k; k and v written to the paged cache [block][16][n_kv][128].
+__global__ void k_rope_cache(__nv_bfloat16 *q, const __nv_bfloat16 *k, const __nv_bfloat16 *v,
+                             const int32_t *pos, const int32_t *req, const int32_t *btab,
+                             int max_blocks, int HQ, int HKV, float theta, __nv_bfloat16 *kc,
+                             __nv_bfloat16 *vc) {
+    const int m = blockIdx.x, head = blockIdx.y, i = threadIdx.x;  // i < 64
+    const int p = pos[m];
+    const float freq = powf(theta, -(float)i / 64.0f);
+    float sn, cs;
+    sincosf((float)p * freq, &sn, &cs);
+    if (head < HQ) {
+        __nv_bfloat16 *qh = q + ((size_t)m * HQ + head) * 128;
+        const float a = __bfloat162float(qh[i]), b = __bfloat162float(qh[i + 64]);
+        qh[i] = __float2bfloat16_rn(a * cs - b * sn);
+        qh[i + 64] = __float2bfloat16_rn(b * cs + a * sn);
+    } else {
+        const int kh = head - HQ;  // < HKV
+        const __nv_bfloat16 *kr = k + ((size_t)m * HKV + kh) * 128;
+        const __nv_bfloat16 *vr = v + ((size_t)m * HKV + kh) * 128;
+        const int blk = btab[(size_t)req[m] * max_blocks + p / 16];
+        const size_t off = (((size_t)blk * 16 + p % 16) * HKV + kh) * 128;
+        const float a = __bfloat162float(kr[i]), b = __bfloat162float(kr[i + 64]);
+        kc[off + i] = __float2bfloat16_rn(a * cs - b * sn);
+        kc[off + i + 64] = __float2bfloat16_rn(b * cs + a * sn);
+        vc[off + i] = vr[i];
+        vc[off + i + 64] = vr[i + 64];
+    }
+}
+
+// Causal attention of one query (token m, head j) over positions 0..pos[m]
+// of its request: 128 threads; keys in chunks of 128 (one per thread), online
+// softmax in FP32; each thread accumulates one output dimension.
+__global__ void __launch_bounds__(128) k_attention(const __nv_bfloat16 *q, const __nv_bfloat16 *kc,
+                                                   const __nv_bfloat16 *vc, const int32_t *pos,
+                                                   const int32_t *req, const int32_t *btab,
+                                                   int max_blocks, int HQ, int HKV, __nv_bfloat16 *out) {
+    const int m = blockIdx.x, j = blockIdx.y, t = threadIdx.x;
+    const int kvh = j / (HQ / HKV);
+    const int n = pos[m] + 1;
+    const int32_t *bt = btab + (size_t)req[m] * max_blocks;
+    __shared__ float qs[128];
+    __shared__ float ps[128];
+    __shared__ float red[4];
+    qs[t] = __bfloat162float(q[((size_t)m * HQ + j) * 128 + t]) * 0.08838834764831845f;  // 1/sqrt(128)
+    __syncthreads();
+    float mx = -FLT_MAX, sum = 0.0f, acc = 0.0f;
+    for (int c0 = 0; c0 < n; c0 += 128) {
+        const int key = c0 + t;
+        float s = -FLT_MAX;
+        if (key < n) {
+            const __nv_bfloat16 *kr = kc + (((size_t)bt[key / 16] * 16 + key % 16) * HKV + kvh) * 128;
+            float d = 0.0f;
+            for (int e = 0; e < 128; e += 8) {
+                const uint4 raw = *reinterpret_cast<const uint4 *>(kr + e);
+                const __nv_bfloat162 *h2 = reinterpret_cast<const __nv_bfloat162 *>(&raw);
+#pragma unroll
+                for (int z = 0; z < 4; ++z) {
+                    const float2 f = __bfloat1622float2(h2[z]);
+                    d = fmaf(qs[e + 2 * z], f.x, d);
+                    d = fmaf(qs[e + 2 * z + 1], f.y, d);
+                }
+            }
+            s = d;
+        }
+        // chunk max
+        float cm = s;
+        for (int o = 16; o; o >>= 1) cm = fmaxf(cm, __shfl_xor_sync(0xffffffffu, cm, o));
+        if ((t & 31) == 0) red[t >> 5] = cm;
+        __syncthreads();
+        cm = fmaxf(fmaxf(red[0], red[1]), fmaxf(red[2], red[3]));
+        __syncthreads();
+        const float nmx = fmaxf(mx, cm);
+        const float scale = expf(mx - nmx);
+        const float p = key < n ? expf(s - nmx) : 0.0f;
+        ps[t] = p;
+        float cs = p;
+        for (int o = 16; o; o >>= 1) cs += __shfl_xor_sync(0xffffffffu, cs, o);
+        if ((t & 31) == 0) red[t >> 5] = cs;
+        __syncthreads();
+        sum = sum * scale + red[0] + red[1] + red[2] + red[3];
+        acc *= scale;
+        const int kn = min(128, n - c0);
+        for (int z = 0; z < kn; ++z) {
+            const int key2 = c0 + z;
+            const __nv_bfloat16 *vr = vc + (((size_t)bt[key2 / 16] * 16 + key2 % 16) * HKV + kvh) * 128;
+            acc = fmaf(ps[z], __bfloat162float(vr[t]), acc);
+        }
+        mx = nmx;
+        __syncthreads();
+    }
+    out[((size_t)m * HQ + j) * 128 + t] = __float2bfloat16_rn(acc / sum);
+}
+
+__global__ void k_add(float *h, const float *y, size_t n) {
+    const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i < n) h[i] += y[i];
+}
+
+__global__ void k_silu_mul(const float *g, const float *u, __nv_bfloat16 *act, size_t n) {
+    const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i < n) {
+        const float a = g[i];
+        act[i] = __float2bfloat16_rn(a / (1.0f + expf(-a)) * u[i]);
+    }
+}
+
+// greedy sampling: first index of the maximum logit
+__global__ void k_argmax(const float *logits, int V, int32_t *out) {
+    const int m = blockIdx.x;
+    const float *l = logits + (size_t)m * V;
+    float best = -FLT_MAX;
+    int bi = 0;
+    for (int c = threadIdx.x; c < V; c += blockDim.x)
+        if (l[c] > best) { best = l[c]; bi = c; }
+    __shared__ float bv[32];
+    __shared__ int bidx[32];
+    for (int o = 16; o; o >>= 1) {
+        const float ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+    }
+    if ((threadIdx.x & 31) == 0) { bv[threadIdx.x >> 5] = best; bidx[threadIdx.x >> 5] = bi; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+            if (bv[w] > best || (bv[w] == best && bidx[w] < bi)) { best = bv[w]; bi = bidx[w]; }
+        out[m] = bi;
+    }
+}
+
+cloak_status serve_step_run(cloak_ctx *ctx, const cloak_serve_desc *d, const cloak_serve_batch *b,
+                            cudaStream_t s) {
+    const cloak_stack_desc &sd = d->stack;
+    if (ctx->dtype != CLOAK_BF16 || sd.head_dim != 128) return CLOAK_E_UNSUPPORTED;
+    const int M = b->num_tokens, S = b->num_sample;
+    if (M < 1 || S < 0 || S > M || !b->token_ids || !b->positions || !b->req_slots || !b->block_tables)
+        return CLOAK_E_INVAL;
+    const int D = sd.d_model, F = sd.d_ff, HQ = sd.n_heads, HKV = sd.n_kv_heads, V = d->vocab;
+    const int QD = HQ * 128, KD = HKV * 128;
+    if (d->lm_head < 0 || d->lm_head >= (int)ctx->tensors.size() || ctx->tensors[d->lm_head].n != V ||
+        ctx->tensors[d->lm_head].k != D)
+        return CLOAK_E_INVAL;
+    const int flags = (b->flags & CLOAK_LINEAR_UNCLOAKED);
+    // workspace: h, y (fp32 [M, max(D, F)]), g, u (fp32 [M, F]), x, attn, q, k, v, act (bf16), logits
+    const size_t Mz = (size_t)M;
+    auto r256 = [](size_t n) { return (n + 255) & ~(size_t)255; };
+    const size_t need = r256(Mz * D * 4) + r256(Mz * D * 4) + 2 * r256(Mz * F * 4) + r256(Mz * D * 2) +
+                        r256(Mz * QD * 2) * 2 + 2 * r256(Mz * KD * 2) + r256(Mz * F * 2) +
+                        r256((size_t)std::max(S, 1) * V * 4) + r256((size_t)std::max(S, 1) * D * 2);
+    if (need > ctx->serve_ws_cap) {
+        if (ctx->d_serve_ws) CLOAK_CUDA(ctx, cudaFree(ctx->d_serve_ws));
+        ctx->d_serve_ws = nullptr;
+        CLOAK_CUDA(ctx, cudaMalloc(&ctx->d_serve_ws, need));
+        ctx->serve_ws_cap = need;
+    }
+    uint8_t *w = (uint8_t *)ctx->d_serve_ws;
+    auto take = [&](size_t n) { uint8_t *p = w; w += r256(n); return p; };
+    float *h = (float *)take(Mz * D * 4);
+    float *y = (float *)take(Mz * D * 4);
+    float *g = (float *)take(Mz * F * 4);
+    float *u = (float *)take(Mz * F * 4);
+    __nv_bfloat16 *x = (__nv_bfloat16 *)take(Mz * D * 2);
+    __nv_bfloat16 *q = (__nv_bfloat16 *)take(Mz * QD * 2);
+    __nv_bfloat16 *attn = (__nv_bfloat16 *)take(Mz * QD * 2);
+    __nv_bfloat16 *k = (__nv_bfloat16 *)take(Mz * KD * 2);
+    __nv_bfloat16 *v = (__nv_bfloat16 *)take(Mz * KD * 2);
+    __nv_bfloat16 *act = (__nv_bfloat16 *)take(Mz * F * 2);
+    float *logits = b->out_logits ? b->out_logits : (float *)take((size_t)std::max(S, 1) * V * 4);
+    __nv_bfloat16 *xs = (__nv_bfloat16 *)take((size_t)std::max(S, 1) * D * 2);
+    cloak_status rc;
+    k_embed<<<M, 256, 0, s>>>((const __nv_bfloat16 *)d->embedding, b->token_ids, D, h);
+    CLOAK_LAUNCHED(ctx);
+    for (int l = 0; l < sd.num_layers; ++l) {
+        const int32_t *lt = sd.layer_tensors + 7 * l;
+        __nv_bfloat16 *kc = (__nv_bfloat16 *)d->k_cache + (size_t)l * d->num_blocks * 16 * KD;
+        __nv_bfloat16 *vc = (__nv_bfloat16 *)d->v_cache + (size_t)l * d->num_blocks * 16 * KD;
+        k_rmsnorm<<<M, 256, 0, s>>>(h, nullptr, D, sd.rms_eps, x);
+        CLOAK_LAUNCHED(ctx);
+        {
+            const int32_t ts[3] = {lt[0], lt[1], lt[2]};
+            const void *xs3[3] = {x, x, x};
+            void *ys3[3] = {q, k, v};
+            if ((rc = linear_batch_run(ctx, 3, ts, xs3, ys3, M, CLOAK_OUT_BF16, flags, s))) return rc;
+        }
+        k_rope_cache<<<dim3(M, HQ + HKV), 64, 0, s>>>(q, k, v, b->positions, b->req_slots, b->block_tables,
+                                                      d->max_blocks, HQ, HKV, d->rope_theta, kc, vc);
+        CLOAK_LAUNCHED(ctx);
+        k_attention<<<dim3(M, HQ), 128, 0, s>>>(q, kc, vc, b->positions, b->req_slots, b->block_tables,
+                                                 d->max_blocks, HQ, HKV, attn);
+        CLOAK_LAUNCHED(ctx);
+        if ((rc = linear_run(ctx, lt[3], attn, y, M, CLOAK_OUT_F32, flags, s))) return rc;
+        k_add<<<nb(Mz * D), 256, 0, s>>>(h, y, Mz * D);
+        CLOAK_LAUNCHED(ctx);
+        k_rmsnorm<<<M, 256, 0, s>>>(h, nullptr, D, sd.rms_eps, x);
+        CLOAK_LAUNCHED(ctx);
+        {
+            const int32_t ts[2] = {lt[4], lt[5]};
+            const void *xs2[2] = {x, x};
+            void *ys2[2] = {g, u};
+            if ((rc = linear_batch_run(ctx, 2, ts, xs2, ys2, M, CLOAK_OUT_F32, flags, s))) return rc;
+        }
+        k_silu_mul<<<nb(Mz * F), 256, 0, s>>>(g, u, act, Mz * F);
+        CLOAK_LAUNCHED(ctx);
+        if ((rc = linear_run(ctx, lt[6], act, y, M, CLOAK_OUT_F32, flags, s))) return rc;
+        k_add<<<nb(Mz * D), 256, 0, s>>>(h, y, Mz * D);
+        CLOAK_LAUNCHED(ctx);
+    }
+    if (S > 0) {
+        k_rmsnorm<<<S, 256, 0, s>>>(h, b->sample_rows, D, sd.rms_eps, xs);
+        CLOAK_LAUNCHED(ctx);
+        if ((rc = linear_run(ctx, d->lm_head, xs, logits, S, CLOAK_OUT_F32, flags, s))) return rc;
+        k_argmax<<<S, 256, 0, s>>>(logits, V, b->out_tokens);
+        CLOAK_LAUNCHED(ctx);
+    }
+    return CLOAK_OK;
+}
+
+}  // namespace cloak

@@ -26,7 +26,7 @@ DTYPE_SIZE = {DT_F32: 4, DT_BF16: 2, DT_E4M3: 1}
 DTYPE_NAME = {DT_F32: "f32", DT_BF16: "bf16", DT_E4M3: "e4m3"}
 
 # tensor kinds (informational; the layer-stack launch uses them to wire stages)
-K_W1, K_W2, K_Q, K_K, K_V, K_O, K_GATE, K_UP, K_DOWN = range(9)
+K_W1, K_W2, K_Q, K_K, K_V, K_O, K_GATE, K_UP, K_DOWN, K_LMHEAD = range(10)
 
 
 @dataclass
@@ -64,6 +64,7 @@ class Model:
     n_kv_heads: int = 0
     head_dim: int = 128
     d_ff: int = 0
+    vocab: int = 0
 
     @property
     def tile_bytes(self) -> int:
@@ -149,6 +150,19 @@ def gqa28_fp8(n_layers=28) -> Model:
                    name=f"gqa3584_e4m3_{n_layers}L", spare_pages=64)
 
 
+def with_lm_head(model: Model, vocab: int) -> Model:
+    """Append an output projection [vocab, d_model] (its own layer index,
+    not permuted: the residual stream keeps its order)."""
+    model.tensors.append(Tensor(vocab, model.d_model, model.num_layers, K_LMHEAD))
+    model.vocab = vocab
+    return model
+
+
+def serving_model(n_layers=32, vocab=32000) -> Model:
+    """The served model: the 7B-class BF16 stack plus a 32,000-token lm_head."""
+    return with_lm_head(llama7b_layer(n_layers), vocab)
+
+
 def small_decoder(n_layers=2, dtype=DT_BF16, d_model=256, n_heads=4,
                   n_kv_heads=2, d_ff=384, head_dim=64, spare_pages=3,
                   page_bytes=None) -> Model:
@@ -185,6 +199,32 @@ def int_weights_host(model: Model, seed: int, lo=-2, hi=2):
     rng = np.random.default_rng(seed)
     return [rng.integers(lo, hi + 1, size=(t.n, t.k)).astype(np.float32)
             for t in model.tensors]
+
+
+def embedding_host(vocab: int, d_model: int, seed: int = 5, std: float = 1.0):
+    """Token embedding table [vocab, d_model], FP32 N(0, std)."""
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal((vocab, d_model), dtype=np.float32) * np.float32(std)
+
+
+def requests_poisson(rate: float, duration: float, vocab: int, seed: int = 0,
+                     prompt_median: int = 1024, prompt_sigma: float = 0.8,
+                     prompt_min: int = 128, prompt_max: int = 4096,
+                     out_min: int = 64, out_max: int = 1024):
+    """Serving workload: Poisson arrivals at `rate` req/s over `duration` s,
+    prompt lengths lognormal (median `prompt_median`) clipped to
+    [prompt_min, prompt_max], output lengths uniform in [out_min, out_max],
+    prompt tokens uniform over the vocabulary. Returns (arrival_s, prompt
+    ndarray, max_new_tokens) tuples in arrival order."""
+    rng = np.random.default_rng(seed)
+    out, t = [], 0.0
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t >= duration:
+            break
+        n = int(np.clip(np.exp(rng.normal(np.log(prompt_median), prompt_sigma)), prompt_min, prompt_max))
+        out.append((t, rng.integers(0, vocab, n, dtype=np.int32), int(rng.integers(out_min, out_max + 1))))
+    return out
 
 
 def weights_device(model: Model, tensor_index: int, seed: int = 0,

@@ -1,0 +1,112 @@
+"""GPU serving step and loop: logits against the FP64 full-model oracle
+(normwise 1e-2), a request's results identical alone and in a mixed batch,
+and the continuous-batching loop serving a workload to completion with
+re-keys in between."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2606_18400_gb300 import serve, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def small_served(layers=2):
+    m = synth.small_decoder(layers, synth.DT_BF16, d_model=512, n_heads=4, n_kv_heads=2, d_ff=384,
+                            head_dim=128, spare_pages=3)
+    return synth.with_lm_head(m, 1000)
+
+
+@pytest.fixture(scope="module")
+def served(cloak_lib):
+    m = small_served()
+    Ws = synth.weights_host(m, seed=0, std=0.05)
+    sm = serve.ServedModel(m, kv_blocks=256, max_blocks=32, twin=True, weights=Ws)
+    yield m, Ws, sm
+    sm.close()
+
+
+def run_steps(sm, seqs, uncloaked=False):
+    """Prefill each (slot, tokens) fully in one step, then decode 3 steps
+    feeding back greedy tokens; returns per slot the list of logits."""
+    dev = "cuda"
+    bt = torch.zeros((8, sm.max_blocks), dtype=torch.int32, device=dev)
+    for slot, toks in seqs:
+        bt[slot] = torch.arange(slot * sm.max_blocks, (slot + 1) * sm.max_blocks, dtype=torch.int32)
+    state = {slot: list(toks) for slot, toks in seqs}
+    logits = {slot: [] for slot, _ in seqs}
+    first = True
+    for step in range(4):
+        ids, pos, req, samp = [], [], [], []
+        for slot, toks in seqs:
+            seq = state[slot]
+            if first:
+                for i, t in enumerate(seq):
+                    ids.append(t); pos.append(i); req.append(slot)
+            else:
+                ids.append(seq[-1]); pos.append(len(seq) - 1); req.append(slot)
+            samp.append(len(ids) - 1)
+        first = False
+        T = lambda a: torch.tensor(a, dtype=torch.int32, device=dev)
+        out = torch.zeros(len(samp), dtype=torch.int32, device=dev)
+        lg = torch.zeros((len(samp), sm.model.vocab), dtype=torch.float32, device=dev)
+        sm.step(T(ids), T(pos), T(req), bt, T(samp), out, lg, uncloaked=uncloaked)
+        torch.cuda.synchronize()
+        for k, (slot, _) in enumerate(seqs):
+            logits[slot].append(lg[k].cpu().numpy())
+            state[slot].append(int(out[k]))
+    return logits, state
+
+
+def test_serve_step_matches_full_model_oracle(served):
+    m, Ws, sm = served
+    toks = list(np.random.default_rng(1).integers(0, 1000, 23))
+    logits, state = run_steps(sm, [(0, toks)])
+    W64 = [O.bf16_value(O.bf16_bits(w)) for w in Ws]
+    emb64 = O.bf16_value(O.bf16_bits(synth.embedding_host(1000, 512)))
+    seq = state[0]
+    ref = O.transformer_logits_f64(m, W64, emb64, seq[:-1])
+    for step, lg in enumerate(logits[0]):
+        p = 22 + step  # position whose next token was sampled
+        assert O.relative_error(lg, ref[p]) <= 1e-2, (step, O.relative_error(lg, ref[p]))
+        top = np.sort(ref[p])[-2:]
+        if top[1] - top[0] > 0.05 * np.std(ref[p]):
+            assert seq[23 + step] == int(np.argmax(ref[p]))
+
+
+def test_request_alone_equals_request_in_a_mix(served):
+    m, Ws, sm = served
+    rng = np.random.default_rng(2)
+    a = list(rng.integers(0, 1000, 17))
+    b = list(rng.integers(0, 1000, 40))
+    c = list(rng.integers(0, 1000, 5))
+    alone, sa = run_steps(sm, [(0, a)])
+    mixed, sm_ = run_steps(sm, [(1, b), (0, a), (2, c)])
+    for x, y in zip(alone[0], mixed[0]):
+        assert np.array_equal(x, y)
+    assert sa[0] == sm_[0]
+    unc, su = run_steps(sm, [(0, a)], uncloaked=True)
+    for x, y in zip(alone[0], unc[0]):
+        assert np.array_equal(x, y)
+
+
+def test_server_serves_a_workload_with_rekeys(cloak_lib):
+    m = small_served()
+    Ws = synth.weights_host(m, seed=0, std=0.05)
+    work = [(0.01 * i, np.random.default_rng(10 + i).integers(0, 1000, 20 + 7 * i).astype(np.int32), 4 + i % 5)
+            for i in range(10)]
+    outs = []
+    for period in (None, 0.02):
+        sm = serve.ServedModel(m, kv_blocks=128, max_blocks=16, weights=Ws)
+        srv = serve.Server(sm, max_running=4, token_budget=64, rekey_period=period)
+        done, wall = srv.run(work)
+        assert len(done) == 10 and all(len(r.out) == r.max_new for r in done)
+        st = serve.latency_stats(done, wall)
+        assert st["tokens"] == sum(w[2] for w in work) and st["ttft_p50_s"] is not None
+        outs.append({r.rid: r.out for r in done})
+        if period:
+            assert len(srv.rekeys) >= 1
+        assert sm.cm.device_status() == 0
+        sm.close()
+    assert outs[0] == outs[1]  # continuous batching and re-keys do not change results
