@@ -562,6 +562,50 @@ def run_cloak(args):
         dist.destroy_process_group()
 
 
+def run_serve(args):
+    """Serving workload: the 32-layer cloaked BF16 model with a 32,000-token
+    lm_head, Poisson arrivals, lognormal prompts clipped to [128, 4096],
+    outputs uniform in [64, 1024], continuous batching admitted by free KV
+    blocks, re-key every 30 s between steps; cloaked vs uncloaked at the same
+    arrival rates. One JSON line per run of the whole sweep."""
+    import torch
+    from paper_2606_18400_gb300 import cloak, serve, synth
+    cloak.load()
+    torch.cuda.set_device(0)
+    model = synth.serving_model(32, 32000)
+    sm = serve.ServedModel(model, kv_blocks=args.kv_blocks, max_blocks=(4096 + 1024) // 16 + 1, twin=True)
+    rates = [float(r) for r in args.rates.split(",")]
+    results = {}
+    clocks = ClockSampler(0)
+    for rate in rates:
+        work = synth.requests_poisson(rate, args.serve_seconds, 32000, seed=int(rate * 10))
+        row = {}
+        for name, unc in (("cloaked", False), ("uncloaked", True)):
+            srv = serve.Server(sm, max_running=64, token_budget=2048, rekey_period=30.0, uncloaked=unc)
+            done, wall = srv.run(work, max_wall=args.serve_seconds + args.drain_seconds)
+            st = serve.latency_stats(done, wall)
+            st["submitted"] = len(work)
+            st["steps"] = srv.steps
+            st["mean_step_tokens"] = float(np.mean(srv.step_tokens)) if srv.step_tokens else 0.0
+            st["rekeys"] = len(srv.rekeys)
+            st["rekey_ms"] = [round(x * 1e3, 2) for x in srv.rekeys]
+            row[name] = st
+        results[str(rate)] = row
+    clk = clocks.stop()
+    assert sm.cm.device_status() == 0
+    sm.close()
+    tps = {r: results[r]["cloaked"]["tokens_per_s"] for r in results}
+    line = {"metric": "serving tokens/s (cloaked 7B-class BF16 model, continuous batching)",
+            "value": max(tps.values()), "unit": "tokens/s", "n_gpus": 1,
+            "higher_is_better": True, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": f"Poisson {args.rates} req/s for {args.serve_seconds} s each (+ up to "
+                                   f"{args.drain_seconds} s drain), prompts lognormal median 1024 clipped "
+                                   f"[128, 4096], outputs U[64, 1024], 32 layers + vocab 32000, "
+                                   f"KV pool {args.kv_blocks} blocks of 16 tokens, re-key every 30 s"},
+            "sweep": results, "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -572,10 +616,17 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--serve", action="store_true", help="run the serving sweep instead")
+    ap.add_argument("--rates", default="2,8,32")
+    ap.add_argument("--serve-seconds", type=float, default=30.0)
+    ap.add_argument("--drain-seconds", type=float, default=30.0)
+    ap.add_argument("--kv-blocks", type=int, default=7000)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
-    if args.impl == "reference":
+    if args.serve:
+        run_serve(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_cloak(args)
