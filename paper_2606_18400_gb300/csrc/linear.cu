@@ -382,30 +382,41 @@ __global__ void __launch_bounds__(192, 1)
                 asm volatile("bar.sync 1, 128;" ::: "memory");
                 const uint32_t c_first = cta_of_unit(rs, G, T), c_last = cta_of_unit(re - 1, G, T);
                 if (et == 0) {
-                    __threadfence();
-                    const uint32_t pieces = c_last - c_first + 1;
-                    const uint32_t old = atomicAdd(P.rowcnt + l.nt, 1u);
-                    __threadfence();
-                    *last_flag = (old == pieces - 1) ? 1u : 0u;
+                    const uint32_t old = atom_add_acq_rel(P.rowcnt + l.nt, 1u);
+                    *last_flag = (old == c_last - c_first) ? 1u : 0u;
                 }
                 asm volatile("bar.sync 1, 128;" ::: "memory");
                 if (*last_flag) {
+                    // piece of CTA c: its first segment (slot 0) unless c is the
+                    // first CTA and started in an earlier row (slot 1)
+                    const int ps_first = ((uint64_t)c_first * T / G < rs) ? 1 : 0;
 #pragma unroll 1
                     for (int c0 = 0; c0 < NPAD; c0 += 16) {
                         float acc[16];
 #pragma unroll
                         for (int j = 0; j < 16; ++j) acc[j] = 0.0f;
-                        for (uint32_t c = c_first; c <= c_last; ++c) {
-                            const Loc lc = locate(b, (uint64_t)c * T / G);
-                            const int ps = (lc.p == l.p && lc.nt == l.nt) ? 0 : 1;
-                            const float *pp = b.part + (((uint64_t)c * 2 + ps) * 128 + r_in) * NPAD + c0;
+                        for (uint32_t cb = c_first; cb <= c_last; cb += 4) {
+                            // all loads of four pieces in flight, then the sums in order
+                            float4 v[4][4];
 #pragma unroll
-                            for (int j = 0; j < 16; j += 4) {
-                                float4 t4 = __ldcg(reinterpret_cast<const float4 *>(pp + j));
-                                acc[j] += t4.x;
-                                acc[j + 1] += t4.y;
-                                acc[j + 2] += t4.z;
-                                acc[j + 3] += t4.w;
+                            for (int q = 0; q < 4; ++q) {
+                                const uint32_t c = cb + q;
+                                if (c > c_last) break;
+                                const int ps = (c == c_first) ? ps_first : 0;
+                                const float *pp = b.part + (((uint64_t)c * 2 + ps) * 128 + r_in) * NPAD + c0;
+#pragma unroll
+                                for (int j = 0; j < 4; ++j) v[q][j] = __ldcg(reinterpret_cast<const float4 *>(pp) + j);
+                            }
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) {
+                                if (cb + q > c_last) break;
+#pragma unroll
+                                for (int j = 0; j < 4; ++j) {
+                                    acc[4 * j] += v[q][j].x;
+                                    acc[4 * j + 1] += v[q][j].y;
+                                    acc[4 * j + 2] += v[q][j].z;
+                                    acc[4 * j + 3] += v[q][j].w;
+                                }
                             }
                         }
                         if (row < P.N) {

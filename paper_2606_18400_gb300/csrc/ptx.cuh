@@ -34,6 +34,15 @@ CLOAK_DEV uint32_t cta_of_unit(uint64_t u, uint64_t G, uint64_t T) {
     return (uint32_t)(((u + 1) * G - 1) / T);
 }
 
+// Arrival on a split row's counter: releases the partial sums this CTA's
+// epilogue threads stored before their named barrier (cumulativity) and
+// acquires those of the CTAs that arrived before.
+CLOAK_DEV uint32_t atom_add_acq_rel(uint32_t *p, uint32_t v) {
+    uint32_t old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
 // ------------------------------------------------------------------ mbarrier
 CLOAK_DEV void mbar_init(uint64_t *bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));

@@ -436,29 +436,45 @@ __global__ void __launch_bounds__(192, 1)
                         uint32_t pieces = 0;
                         for (uint32_t c = c_first; c <= c_last; ++c)
                             pieces += ((uint64_t)c * T / G < ((uint64_t)c + 1) * T / G) ? 1u : 0u;
-                        __threadfence();
-                        const uint32_t old = atomicAdd(P.rowcnt + l.nt, 1u);
-                        __threadfence();
+                        const uint32_t old = atom_add_acq_rel(P.rowcnt + l.nt, 1u);
                         *last_flag = (old == pieces - 1) ? 1u : 0u;
                     }
                     asm volatile("bar.sync 1, 128;" ::: "memory");
                     if (*last_flag) {
+                        const int ps_first = ((uint64_t)c_first * T / G < rs) ? 1 : 0;
 #pragma unroll 1
                         for (int c0 = 0; c0 < NPAD; c0 += 16) {
                             float ag[16], au[16];
 #pragma unroll
                             for (int j = 0; j < 16; ++j) ag[j] = au[j] = 0.0f;
-                            for (uint32_t c = c_first; c <= c_last; ++c) {
-                                if ((uint64_t)c * T / G >= ((uint64_t)c + 1) * T / G) continue;
-                                const SLoc lc = sloc(st, (uint64_t)c * T / G);
-                                const int ps = (lc.p == l.p && lc.nt == l.nt) ? 0 : 1;
-                                const float *pp = a.part + ((((uint64_t)c * 2 + ps) * 2) * 128 + r_in) * NPAD + c0;
+                            for (uint32_t cb = c_first; cb <= c_last; cb += 4) {
+                                // all loads of up to four pieces in flight, then the
+                                // sums in CTA order
+                                float4 vg4[4][4], vu4[4][4];
+                                bool has[4];
 #pragma unroll
-                                for (int j = 0; j < 16; j += 4) {
-                                    const float4 t4 = __ldcg(reinterpret_cast<const float4 *>(pp + j));
-                                    ag[j] += t4.x; ag[j + 1] += t4.y; ag[j + 2] += t4.z; ag[j + 3] += t4.w;
-                                    const float4 t5 = __ldcg(reinterpret_cast<const float4 *>(pp + 128 * NPAD + j));
-                                    au[j] += t5.x; au[j + 1] += t5.y; au[j + 2] += t5.z; au[j + 3] += t5.w;
+                                for (int q = 0; q < 4; ++q) {
+                                    const uint32_t c = cb + q;
+                                    has[q] = c <= c_last && ((uint64_t)c * T / G < ((uint64_t)c + 1) * T / G);
+                                    if (!has[q]) continue;
+                                    const int ps = (c == c_first) ? ps_first : 0;
+                                    const float *pp = a.part + ((((uint64_t)c * 2 + ps) * 2) * 128 + r_in) * NPAD + c0;
+#pragma unroll
+                                    for (int j = 0; j < 4; ++j) {
+                                        vg4[q][j] = __ldcg(reinterpret_cast<const float4 *>(pp) + j);
+                                        vu4[q][j] = __ldcg(reinterpret_cast<const float4 *>(pp + 128 * NPAD) + j);
+                                    }
+                                }
+#pragma unroll
+                                for (int q = 0; q < 4; ++q) {
+                                    if (!has[q]) continue;
+#pragma unroll
+                                    for (int j = 0; j < 4; ++j) {
+                                        ag[4 * j] += vg4[q][j].x; ag[4 * j + 1] += vg4[q][j].y;
+                                        ag[4 * j + 2] += vg4[q][j].z; ag[4 * j + 3] += vg4[q][j].w;
+                                        au[4 * j] += vu4[q][j].x; au[4 * j + 1] += vu4[q][j].y;
+                                        au[4 * j + 2] += vu4[q][j].z; au[4 * j + 3] += vu4[q][j].w;
+                                    }
                                 }
                             }
                             if (row < P.N) {
