@@ -58,6 +58,8 @@ struct StackArgs {
     float *h;                 // FP32 residual [M, D]
     __nv_bfloat16 *hb;        // its BF16 copy (the activation operand)
     float *part;              // [grid][2][2][128][NPAD]
+    float *ss_part;           // [grid][64]: per CTA, sum of squares of the residual rows it finalised
+    const float *ss_init;     // [64]: sum of squares of the input residual
     unsigned int *bar;        // grid barrier arrivals (zeroed before launch)
     int *abort;               // set by a CTA that gave up (zeroed before launch)
     int *status;
@@ -166,6 +168,23 @@ __device__ __forceinline__ void fence_proxy_async_global() {
 
 __device__ __forceinline__ float silu(float g) { return g / (1.0f + expf(-g)); }
 
+// Add this chunk's squares of the finalised residual values (hsq[j] for
+// token c0 + j, 0 where the thread wrote nothing) to the CTA's running sums:
+// warp sums, then the four warps in fixed order (deterministic).
+__device__ __forceinline__ void accumulate_squares(float (&hsq)[16], int c0, int qd, int lane, int et,
+                                                   float *ss_w, float *ss_acc) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+        for (int o = 16; o; o >>= 1) hsq[j] += __shfl_xor_sync(0xffffffffu, hsq[j], o);
+    if (lane == 0) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) ss_w[qd * 16 + j] = hsq[j];
+    }
+    asm volatile("bar.sync 1, 128;" ::: "memory");
+    if (et < 16) ss_acc[c0 + et] += ss_w[et] + ss_w[16 + et] + ss_w[32 + et] + ss_w[48 + et];
+    asm volatile("bar.sync 1, 128;" ::: "memory");
+}
+
 template <int NPAD>
 __global__ void __launch_bounds__(192, 1)
     k_stack_tc(const __grid_constant__ CUtensorMap tw, const __grid_constant__ StackMaps xm,
@@ -181,6 +200,8 @@ __global__ void __launch_bounds__(192, 1)
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tempty + 2);
     volatile uint32_t *last_flag = tmem_slot + 1;
     float *rstd = reinterpret_cast<float *>(tmem_slot + 4);  // [NPAD]
+    float *ss_acc = rstd + 64;                                 // [NPAD] this CTA's sums of squares
+    float *ss_w = ss_acc + 64;                                 // [4][16] per-warp chunk sums
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint64_t G = gridDim.x;
@@ -356,19 +377,23 @@ __global__ void __launch_bounds__(192, 1)
                 if (!*last_flag) { ok = false; break; }
             }
             if (st.need_rstd) {
-                // r_m = 1 / sqrt(mean(h_m^2) + eps), one warp per token
-                for (int m = qd; m < a.M; m += 4) {
-                    const float *hr = a.h + (size_t)m * a.D;
+                // r_m = 1 / sqrt(mean(h_m^2) + eps); the sum of squares is the
+                // input's (first stage) or the per-CTA sums of the residual rows
+                // finalised in the previous stage, added in CTA order
+                if (et < a.M) {
                     float ss = 0.0f;
-                    for (int c = lane * 4; c < a.D; c += 128) {
-                        const float4 v = __ldcg(reinterpret_cast<const float4 *>(hr + c));
-                        ss += v.x * v.x + v.y * v.y + v.z * v.z + v.w * v.w;
+                    if (si == 0) {
+                        ss = a.ss_init[et];
+                    } else {
+#pragma unroll 8
+                        for (uint32_t c = 0; c < (uint32_t)G; ++c) ss += __ldcg(a.ss_part + (size_t)c * 64 + et);
                     }
-                    for (int o = 16; o; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-                    if (lane == 0) rstd[m] = rsqrtf(ss / (float)a.D + a.eps);
+                    rstd[et] = rsqrtf(ss / (float)a.D + a.eps);
                 }
                 asm volatile("bar.sync 1, 128;" ::: "memory");
             }
+            if (et < 64) ss_acc[et] = 0.0f;
+            asm volatile("bar.sync 1, 128;" ::: "memory");
             const SLoc first = (u0 < u1) ? sloc(st, u0) : SLoc{0, 0, 0, 0, 0};
             for (uint64_t u = u0; u < u1; ++seg) {
                 const SLoc l = sloc(st, u);
@@ -398,6 +423,9 @@ __global__ void __launch_bounds__(192, 1)
                         if (!has_u) vu[j] = 0.0f;
                     }
                     if (full_row) {
+                        float hsq[16];
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) hsq[j] = 0.0f;
                         if (row < P.N) {
 #pragma unroll
                             for (int j = 0; j < 16; ++j) {
@@ -410,11 +438,13 @@ __global__ void __launch_bounds__(192, 1)
                                     const float hn = a.h[o] + vg[j];
                                     a.h[o] = hn;
                                     a.hb[o] = __float2bfloat16_rn(hn);
+                                    hsq[j] = hn * hn;
                                 } else {
                                     P.out[o] = __float2bfloat16_rn(silu(vg[j] * rstd[m]) * (vu[j] * rstd[m]));
                                 }
                             }
                         }
+                        if (P.mode == MODE_RESID) accumulate_squares(hsq, c0, qd, lane, et, ss_w, ss_acc);
                     } else {
 #pragma unroll
                         for (int j = 0; j < 16; j += 4) {
@@ -477,6 +507,9 @@ __global__ void __launch_bounds__(192, 1)
                                     }
                                 }
                             }
+                            float hsq[16];
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) hsq[j] = 0.0f;
                             if (row < P.N) {
 #pragma unroll
                                 for (int j = 0; j < 16; ++j) {
@@ -489,18 +522,22 @@ __global__ void __launch_bounds__(192, 1)
                                         const float hn = a.h[o] + ag[j];
                                         a.h[o] = hn;
                                         a.hb[o] = __float2bfloat16_rn(hn);
+                                        hsq[j] = hn * hn;
                                     } else {
                                         P.out[o] = __float2bfloat16_rn(silu(ag[j] * rstd[m]) * (au[j] * rstd[m]));
                                     }
                                 }
                             }
+                            if (P.mode == MODE_RESID) accumulate_squares(hsq, c0, qd, lane, et, ss_w, ss_acc);
                         }
                         if (et == 0) P.rowcnt[l.nt] = 0;
                     }
                 }
                 u = send;
             }
-            // this CTA's outputs of the stage are written: arrive
+            // this CTA's outputs of the stage are written (and, after a residual
+            // update, its sums of squares): arrive
+            if (st.p[0].mode == MODE_RESID && et < 64) a.ss_part[(size_t)blockIdx.x * 64 + et] = ss_acc[et];
             asm volatile("bar.sync 1, 128;" ::: "memory");
             if (et == 0) {
                 fence_proxy_async_global();
@@ -520,9 +557,24 @@ __global__ void __launch_bounds__(192, 1)
 
 // --------------------------------------------------------------------- host
 
-__global__ void k_f32_to_bf16(const float *x, __nv_bfloat16 *y, size_t n) {
-    size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    if (i < n) y[i] = __float2bfloat16_rn(x[i]);
+// BF16 copy of the input residual and its per-token sum of squares
+__global__ void k_stack_input(const float *h, int D, __nv_bfloat16 *hb, float *ss) {
+    const int m = blockIdx.x;
+    float acc = 0.0f;
+    for (int c = threadIdx.x; c < D; c += blockDim.x) {
+        const float v = h[(size_t)m * D + c];
+        hb[(size_t)m * D + c] = __float2bfloat16_rn(v);
+        acc += v * v;
+    }
+    __shared__ float red[32];
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.0f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        ss[m] = t;
+    }
 }
 
 template <int NPAD>
@@ -587,7 +639,7 @@ cloak_status stack_decode_run(cloak_ctx *ctx, const cloak_stack_desc *d, float *
     auto r256 = [](size_t n) { return (n + 255) & ~(size_t)255; };
     const size_t bytes = r256((size_t)M * D * 2) + r256((size_t)M * HQ * 2) + 2 * r256((size_t)M * HKV * 2) +
                          r256((size_t)M * F * 2) + r256(part_floats * 4) + r256(rows * 4) + r256(8) +
-                         r256(nstages * sizeof(StackStage));
+                         r256(nstages * sizeof(StackStage)) + r256((size_t)(G + 1) * 64 * 4);
     (void)act_elems;
     cudaError_t err = cudaSuccess;
     void *before = ctx->d_stack_ws;
@@ -608,6 +660,7 @@ cloak_status stack_decode_run(cloak_ctx *ctx, const cloak_stack_desc *d, float *
     uint32_t *cnt = (uint32_t *)take(rows * 4);
     uint32_t *bar = (uint32_t *)take(8);
     StackStage *dst = (StackStage *)take(nstages * sizeof(StackStage));
+    float *ss = (float *)take((size_t)(G + 1) * 64 * 4);  // [G][64] partials, then [64] input
     // the stage program
     std::vector<StackStage> st(nstages);
     size_t roff = 0;
@@ -665,8 +718,7 @@ cloak_status stack_decode_run(cloak_ctx *ctx, const cloak_stack_desc *d, float *
     }
     CLOAK_CUDA(ctx, cudaMemsetAsync(cnt, 0, rows * 4, s));
     CLOAK_CUDA(ctx, cudaMemsetAsync(bar, 0, 8, s));
-    const size_t n = (size_t)M * D;
-    k_f32_to_bf16<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(h, hb, n);
+    k_stack_input<<<M, 256, 0, s>>>(h, D, hb, ss + (size_t)G * 64);
     CLOAK_LAUNCHED(ctx);
     StackMaps xm;
     if (!encode_tmap_2d(&xm.m[XMAP_H], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, hb, D, M, (uint64_t)D * 2, 64, npad) ||
@@ -685,6 +737,8 @@ cloak_status stack_decode_run(cloak_ctx *ctx, const cloak_stack_desc *d, float *
     a.h = h;
     a.hb = hb;
     a.part = part;
+    a.ss_part = ss;
+    a.ss_init = ss + (size_t)G * 64;
     a.bar = bar;
     a.abort = (int *)(bar + 1);
     a.status = ctx->d_status;
