@@ -256,6 +256,7 @@ __global__ void __launch_bounds__(192, 1)
             const uint64_t u0 = blockIdx.x * T / G, u1 = (blockIdx.x + 1) * T / G;
             const uint32_t target = (uint32_t)(si * G);
             bool passed = (si == 0) || ld_acquire(a.bar) >= target;
+            if (passed && si > 0) fence_proxy_async_global();  // before any TMA read of this stage
             uint32_t cur = stack_slot(a, st, u0 + lane, u1), nxt = stack_slot(a, st, u0 + 32 + lane, u1);
             for (uint64_t u = u0; u < u1; ++u, ++it) {
                 const uint32_t j = (uint32_t)((u - u0) & 31);
@@ -538,9 +539,11 @@ __global__ void __launch_bounds__(192, 1)
             // this CTA's outputs of the stage are written (and, after a residual
             // update, its sums of squares): arrive
             if (st.p[0].mode == MODE_RESID && et < 64) a.ss_part[(size_t)blockIdx.x * 64 + et] = ss_acc[et];
+            // every writer makes its stores visible to the async proxy (the
+            // next stage reads them with TMA), then one release arrival
+            fence_proxy_async_global();
             asm volatile("bar.sync 1, 128;" ::: "memory");
             if (et == 0) {
-                fence_proxy_async_global();
                 __threadfence();
                 atomicAdd(a.bar, 1u);
             }
