@@ -58,7 +58,7 @@ struct StackArgs {
     float *h;                 // FP32 residual [M, D]
     __nv_bfloat16 *hb;        // its BF16 copy (the activation operand)
     float *part;              // [grid][2][2][128][NPAD]
-    float *ss_part;           // [grid][64]: per CTA, sum of squares of the residual rows it finalised
+    float *ss_rows;           // [D/128][64]: per residual row tile, its sum of squares per token
     const float *ss_init;     // [64]: sum of squares of the input residual
     unsigned int *bar;        // grid barrier arrivals (zeroed before launch)
     int *abort;               // set by a CTA that gave up (zeroed before launch)
@@ -168,11 +168,12 @@ __device__ __forceinline__ void fence_proxy_async_global() {
 
 __device__ __forceinline__ float silu(float g) { return g / (1.0f + expf(-g)); }
 
-// Add this chunk's squares of the finalised residual values (hsq[j] for
-// token c0 + j, 0 where the thread wrote nothing) to the CTA's running sums:
-// warp sums, then the four warps in fixed order (deterministic).
-__device__ __forceinline__ void accumulate_squares(float (&hsq)[16], int c0, int qd, int lane, int et,
-                                                   float *ss_w, float *ss_acc) {
+// Sum of squares of a finalised residual row tile for tokens c0..c0+15
+// (hsq[j]: this thread's row, 0 where it wrote nothing): warp sums, then the
+// four warps in fixed order, stored for the tile. Each tile has one
+// finaliser per stage, so the result does not depend on which CTA it is.
+__device__ __forceinline__ void tile_squares(float (&hsq)[16], int c0, int qd, int lane, int et,
+                                             float *ss_w, float *dst) {
 #pragma unroll
     for (int j = 0; j < 16; ++j)
         for (int o = 16; o; o >>= 1) hsq[j] += __shfl_xor_sync(0xffffffffu, hsq[j], o);
@@ -181,7 +182,7 @@ __device__ __forceinline__ void accumulate_squares(float (&hsq)[16], int c0, int
         for (int j = 0; j < 16; ++j) ss_w[qd * 16 + j] = hsq[j];
     }
     asm volatile("bar.sync 1, 128;" ::: "memory");
-    if (et < 16) ss_acc[c0 + et] += ss_w[et] + ss_w[16 + et] + ss_w[32 + et] + ss_w[48 + et];
+    if (et < 16) dst[c0 + et] = ss_w[et] + ss_w[16 + et] + ss_w[32 + et] + ss_w[48 + et];
     asm volatile("bar.sync 1, 128;" ::: "memory");
 }
 
@@ -200,8 +201,7 @@ __global__ void __launch_bounds__(192, 1)
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tempty + 2);
     volatile uint32_t *last_flag = tmem_slot + 1;
     float *rstd = reinterpret_cast<float *>(tmem_slot + 4);  // [NPAD]
-    float *ss_acc = rstd + 64;                                 // [NPAD] this CTA's sums of squares
-    float *ss_w = ss_acc + 64;                                 // [4][16] per-warp chunk sums
+    float *ss_w = rstd + 64;                                   // [4][16] per-warp chunk sums
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint64_t G = gridDim.x;
@@ -379,22 +379,21 @@ __global__ void __launch_bounds__(192, 1)
             }
             if (st.need_rstd) {
                 // r_m = 1 / sqrt(mean(h_m^2) + eps); the sum of squares is the
-                // input's (first stage) or the per-CTA sums of the residual rows
-                // finalised in the previous stage, added in CTA order
+                // input's (first stage) or that of the residual row tiles the
+                // previous stage finalised, added in row order
                 if (et < a.M) {
                     float ss = 0.0f;
                     if (si == 0) {
                         ss = a.ss_init[et];
                     } else {
+                        const int ntiles = a.D / 128;
 #pragma unroll 8
-                        for (uint32_t c = 0; c < (uint32_t)G; ++c) ss += __ldcg(a.ss_part + (size_t)c * 64 + et);
+                        for (int t = 0; t < ntiles; ++t) ss += __ldcg(a.ss_rows + (size_t)t * 64 + et);
                     }
                     rstd[et] = rsqrtf(ss / (float)a.D + a.eps);
                 }
                 asm volatile("bar.sync 1, 128;" ::: "memory");
             }
-            if (et < 64) ss_acc[et] = 0.0f;
-            asm volatile("bar.sync 1, 128;" ::: "memory");
             const SLoc first = (u0 < u1) ? sloc(st, u0) : SLoc{0, 0, 0, 0, 0};
             for (uint64_t u = u0; u < u1; ++seg) {
                 const SLoc l = sloc(st, u);
@@ -445,7 +444,7 @@ __global__ void __launch_bounds__(192, 1)
                                 }
                             }
                         }
-                        if (P.mode == MODE_RESID) accumulate_squares(hsq, c0, qd, lane, et, ss_w, ss_acc);
+                        if (P.mode == MODE_RESID) tile_squares(hsq, c0, qd, lane, et, ss_w, a.ss_rows + (size_t)l.nt * 64);
                     } else {
 #pragma unroll
                         for (int j = 0; j < 16; j += 4) {
@@ -529,7 +528,7 @@ __global__ void __launch_bounds__(192, 1)
                                     }
                                 }
                             }
-                            if (P.mode == MODE_RESID) accumulate_squares(hsq, c0, qd, lane, et, ss_w, ss_acc);
+                            if (P.mode == MODE_RESID) tile_squares(hsq, c0, qd, lane, et, ss_w, a.ss_rows + (size_t)l.nt * 64);
                         }
                         if (et == 0) P.rowcnt[l.nt] = 0;
                     }
@@ -538,7 +537,6 @@ __global__ void __launch_bounds__(192, 1)
             }
             // this CTA's outputs of the stage are written (and, after a residual
             // update, its sums of squares): arrive
-            if (st.p[0].mode == MODE_RESID && et < 64) a.ss_part[(size_t)blockIdx.x * 64 + et] = ss_acc[et];
             // every writer makes its stores visible to the async proxy (the
             // next stage reads them with TMA), then one release arrival
             fence_proxy_async_global();
@@ -642,7 +640,7 @@ cloak_status stack_decode_run(cloak_ctx *ctx, const cloak_stack_desc *d, float *
     auto r256 = [](size_t n) { return (n + 255) & ~(size_t)255; };
     const size_t bytes = r256((size_t)M * D * 2) + r256((size_t)M * HQ * 2) + 2 * r256((size_t)M * HKV * 2) +
                          r256((size_t)M * F * 2) + r256(part_floats * 4) + r256(rows * 4) + r256(8) +
-                         r256(nstages * sizeof(StackStage)) + r256((size_t)(G + 1) * 64 * 4);
+                         r256(nstages * sizeof(StackStage)) + r256((size_t)(D / 128 + 1) * 64 * 4);
     (void)act_elems;
     cudaError_t err = cudaSuccess;
     void *before = ctx->d_stack_ws;
@@ -663,7 +661,7 @@ cloak_status stack_decode_run(cloak_ctx *ctx, const cloak_stack_desc *d, float *
     uint32_t *cnt = (uint32_t *)take(rows * 4);
     uint32_t *bar = (uint32_t *)take(8);
     StackStage *dst = (StackStage *)take(nstages * sizeof(StackStage));
-    float *ss = (float *)take((size_t)(G + 1) * 64 * 4);  // [G][64] partials, then [64] input
+    float *ss = (float *)take((size_t)(D / 128 + 1) * 64 * 4);  // [D/128][64] row tiles, then [64] input
     // the stage program
     std::vector<StackStage> st(nstages);
     size_t roff = 0;
@@ -721,7 +719,7 @@ cloak_status stack_decode_run(cloak_ctx *ctx, const cloak_stack_desc *d, float *
     }
     CLOAK_CUDA(ctx, cudaMemsetAsync(cnt, 0, rows * 4, s));
     CLOAK_CUDA(ctx, cudaMemsetAsync(bar, 0, 8, s));
-    k_stack_input<<<M, 256, 0, s>>>(h, D, hb, ss + (size_t)G * 64);
+    k_stack_input<<<M, 256, 0, s>>>(h, D, hb, ss + (size_t)(D / 128) * 64);
     CLOAK_LAUNCHED(ctx);
     StackMaps xm;
     if (!encode_tmap_2d(&xm.m[XMAP_H], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, hb, D, M, (uint64_t)D * 2, 64, npad) ||
@@ -740,8 +738,8 @@ cloak_status stack_decode_run(cloak_ctx *ctx, const cloak_stack_desc *d, float *
     a.h = h;
     a.hb = hb;
     a.part = part;
-    a.ss_part = ss;
-    a.ss_init = ss + (size_t)G * 64;
+    a.ss_rows = ss;
+    a.ss_init = ss + (size_t)(D / 128) * 64;
     a.bar = bar;
     a.abort = (int *)(bar + 1);
     a.status = ctx->d_status;
