@@ -606,6 +606,42 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def run_profile(args):
+    """Small cases of one kernel each, for ncu captures (a few GB at most):
+    stack  -- a 4-layer 7B-class stack (1.6 GB), decode M=1, 3 launches;
+    fp8    -- one GQA E4M3 layer (233 MB), grouped decode M=1, 3 launches;
+    prefill-- one 7B-class layer, grouped M=512, 3 launches."""
+    import torch
+    from paper_2606_18400_gb300 import cloak, synth
+    cloak.load()
+    torch.cuda.set_device(0)
+    if args.profile == "stack":
+        model = synth.llama7b_layer(4)
+    elif args.profile == "fp8":
+        model = synth.gqa28_fp8(1)
+    else:
+        model = synth.llama7b_layer(1)
+    cm = cloak.CloakModel(model)
+    cm.keygen(KEY, 0)
+    for t in range(len(model.tensors)):
+        cm.shuffle(t, synth.weights_device(model, t, seed=0))
+    torch.cuda.synchronize()
+    if args.profile == "stack":
+        h0 = torch.from_numpy(synth.activations_host(1, 4096, seed=1)).cuda()
+        for _ in range(3):
+            cm.stack_decode(h0.clone())
+    else:
+        M = 1 if args.profile == "fp8" else 512
+        xs = [torch.from_numpy(synth.activations_host(M, t.k, seed=i)).cuda().to(torch.bfloat16)
+              for i, t in enumerate(model.tensors)]
+        for _ in range(3):
+            cm.linear_batch(list(range(len(model.tensors))), xs)
+    torch.cuda.synchronize()
+    assert cm.device_status() == 0
+    cm.close()
+    print(json.dumps({"profile": args.profile, "ok": True}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -617,6 +653,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--serve", action="store_true", help="run the serving sweep instead")
+    ap.add_argument("--profile", choices=["stack", "fp8", "prefill"], help="small case for ncu")
     ap.add_argument("--rates", default="2,8,32")
     ap.add_argument("--serve-seconds", type=float, default=30.0)
     ap.add_argument("--drain-seconds", type=float, default=30.0)
@@ -624,7 +661,9 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
-    if args.serve:
+    if args.profile:
+        run_profile(args)
+    elif args.serve:
         run_serve(args)
     elif args.impl == "reference":
         run_reference(args)
