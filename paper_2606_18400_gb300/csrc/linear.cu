@@ -107,6 +107,7 @@ struct QuantJobs {
 
 // one launch for every problem of a batch: block (r, p) quantises row r of x_p
 __global__ void k_quant_rows_multi(QuantJobs j) {
+    griddep_launch_dependents();  // the linear may start (and fetch weights) now
     const int p = blockIdx.y;
     const int64_t r = blockIdx.x;
     const int K = j.K[p];
@@ -153,6 +154,7 @@ struct TcProblem {
 struct TcBatch {
     const uint32_t *slot_of;  // gather table; nullptr: uncloaked (slot = tile index)
     int np, M, out_f32, relu;
+    int dep_wait;             // launched as a programmatic dependent of the quantiser
     uint64_t total;           // units of all problems
     float *part;              // [grid][2][128][NPAD] partial sums
     int *status;
@@ -264,6 +266,24 @@ __global__ void __launch_bounds__(192, 1)
         Loc l = locate(b, u0);
         uint32_t cur = slot_for(b, u0 + lane, u1), nxt = slot_for(b, u0 + 32 + lane, u1);
         uint32_t it = 0;
+        // as a dependent launch, weight tiles are requested at once; the
+        // activation halves of the first ring slots wait for the quantiser
+        bool waited = !b.dep_wait;
+        int pend_n = 0;
+        int pend_s[16], pend_p[16];
+        int32_t pend_kc[16];
+        auto issue_x = [&](int s, int p, int32_t kc) {
+            uint8_t *sb = smem + s * C::STAGE + C::A_BYTES;
+            const CUtensorMap *xm = &tx.m[p];
+            tma_load_2d_hint(sb, xm, &full[s], kc, 0, pol_x);
+            if (!FP8) tma_load_2d_hint(sb + C::B_BYTES / 2, xm, &full[s], kc + 64, 0, pol_x);
+        };
+        auto release = [&]() {
+            griddep_wait();
+            waited = true;
+            for (int q = 0; q < pend_n; ++q) issue_x(pend_s[q], pend_p[q], pend_kc[q]);
+            pend_n = 0;
+        };
         for (uint64_t u = u0; u < u1; ++u, ++it) {
             const uint32_t j = (uint32_t)((u - u0) & 31);
             if (j == 0 && u > u0) {
@@ -274,23 +294,26 @@ __global__ void __launch_bounds__(192, 1)
             const int s = it % C::STAGES;
             const uint32_t ph = (it / C::STAGES) & 1;
             bool ok = true;
-            if (lane == 0 && it >= (uint32_t)C::STAGES) ok = mbar_wait(&empty[s], ph ^ 1, b.status);
+            if (lane == 0 && it >= (uint32_t)C::STAGES) {
+                if (!waited) release();
+                ok = mbar_wait(&empty[s], ph ^ 1, b.status);
+            }
             if (!__shfl_sync(0xffffffffu, (int)ok, 0)) break;
             const TcProblem &P = b.p[l.p];
             if (lane == 0) {
                 mbar_expect_tx(&full[s], C::STAGE);
                 const int32_t row = (int32_t)(slot * 128u);
                 const int32_t kc = (int32_t)l.kt * 128;
-                uint8_t *sa = smem + s * C::STAGE, *sb = sa + C::A_BYTES;
-                const CUtensorMap *xm = &tx.m[l.p];
-                if (FP8) {
-                    tma_load_2d_hint(sa, &tw, &full[s], 0, row, pol_w);
-                    tma_load_2d_hint(sb, xm, &full[s], kc, 0, pol_x);
+                uint8_t *sa = smem + s * C::STAGE;
+                tma_load_2d_hint(sa, &tw, &full[s], 0, row, pol_w);
+                if (!FP8) tma_load_2d_hint(sa + 16384, &tw, &full[s], 64, row, pol_w);
+                if (waited) {
+                    issue_x(s, l.p, kc);
                 } else {
-                    tma_load_2d_hint(sa, &tw, &full[s], 0, row, pol_w);
-                    tma_load_2d_hint(sa + 16384, &tw, &full[s], 64, row, pol_w);
-                    tma_load_2d_hint(sb, xm, &full[s], kc, 0, pol_x);
-                    tma_load_2d_hint(sb + C::B_BYTES / 2, xm, &full[s], kc + 64, 0, pol_x);
+                    pend_s[pend_n] = s;
+                    pend_p[pend_n] = l.p;
+                    pend_kc[pend_n] = kc;
+                    ++pend_n;
                 }
             }
             // advance (problem, row, column)
@@ -302,6 +325,7 @@ __global__ void __launch_bounds__(192, 1)
                 }
             }
         }
+        if (lane == 0 && !waited) release();
     } else if (warp == 1) {
         if (lane == 0) {
             uint32_t it = 0, seg = 0;
@@ -343,6 +367,7 @@ __global__ void __launch_bounds__(192, 1)
         const int qd = warp & 3;
         const int r_in = qd * 32 + lane;
         const int et = threadIdx.x - 64;  // 0..127
+        if (b.dep_wait) griddep_wait();  // the activation scales come from the quantiser
         const Loc first = locate(b, u0);
         uint32_t seg = 0;
         for (uint64_t u = u0; u < u1; ++seg) {
@@ -468,7 +493,21 @@ static cloak_status launch_tc(cloak_ctx *ctx, const CUtensorMap &tw, const void 
         ctx->part_cap = need;
     }
     b.part = ctx->d_part;
-    k_linear_tc<FP8, NPAD><<<grid, 192, C::SMEM, s>>>(tw, tx, b);
+    if (b.dep_wait) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(192);
+        cfg.dynamicSmemBytes = C::SMEM;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        CLOAK_CUDA(ctx, cudaLaunchKernelEx(&cfg, k_linear_tc<FP8, NPAD>, tw, tx, b));
+    } else {
+        k_linear_tc<FP8, NPAD><<<grid, 192, C::SMEM, s>>>(tw, tx, b);
+    }
     CLOAK_LAUNCHED(ctx);
     return CLOAK_OK;
 }
@@ -561,6 +600,7 @@ cloak_status linear_batch_run(cloak_ctx *ctx, int n, const int32_t *tensors, con
         if (fp8) {
             k_quant_rows_multi<<<dim3(mb, n), 256, 0, s>>>(qj);
             CLOAK_LAUNCHED(ctx);
+            b.dep_wait = 1;
         }
         cloak_status rc = fp8 ? dispatch_tc<true>(ctx, tw, xm, b, s) : dispatch_tc<false>(ctx, tw, xm, b, s);
         if (rc) return rc;

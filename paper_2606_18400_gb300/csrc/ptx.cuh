@@ -43,6 +43,14 @@ CLOAK_DEV uint32_t atom_add_acq_rel(uint32_t *p, uint32_t v) {
     return old;
 }
 
+// Programmatic dependent launch: a primary lets its dependents start early;
+// a dependent waits for its primaries' completion (and memory) before reading
+// their outputs.
+CLOAK_DEV void griddep_launch_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+CLOAK_DEV void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // ------------------------------------------------------------------ mbarrier
 CLOAK_DEV void mbar_init(uint64_t *bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
