@@ -262,6 +262,14 @@ typedef struct {
     const int32_t *token_ids, *positions, *req_slots, *block_tables, *sample_rows;
     int32_t *out_tokens;
     float *out_logits;
+    /* Optional attention work split (device int32; NULL qtiles: one block
+     * per token). qtiles[num_qtiles][3] = (first token, count <= 64, 0): runs
+     * of consecutive tokens of one request at consecutive positions, whose
+     * queries share staged K/V tiles; single_rows[num_single]: the other
+     * tokens, one block each. Together they must cover every token once. A
+     * token's result depends only on which of the two lists holds it. */
+    int32_t num_qtiles, num_single;
+    const int32_t *qtiles, *single_rows;
 } cloak_serve_batch;
 
 /* One forward step of the served model over a mixed batch: per layer

@@ -87,8 +87,9 @@ __global__ void k_rope_cache(__nv_bfloat16 *q, const __nv_bfloat16 *k, const __n
 __global__ void __launch_bounds__(128) k_attention(const __nv_bfloat16 *q, const __nv_bfloat16 *kc,
                                                    const __nv_bfloat16 *vc, const int32_t *pos,
                                                    const int32_t *req, const int32_t *btab,
-                                                   int max_blocks, int HQ, int HKV, __nv_bfloat16 *out) {
-    const int m = blockIdx.x, j = blockIdx.y, t = threadIdx.x;
+                                                   const int32_t *rows, int max_blocks, int HQ, int HKV,
+                                                   __nv_bfloat16 *out) {
+    const int m = rows ? rows[blockIdx.x] : (int)blockIdx.x, j = blockIdx.y, t = threadIdx.x;
     const int kvh = j / (HQ / HKV);
     const int n = pos[m] + 1;
     const int32_t *bt = btab + (size_t)req[m] * max_blocks;
@@ -143,6 +144,117 @@ __global__ void __launch_bounds__(128) k_attention(const __nv_bfloat16 *q, const
         __syncthreads();
     }
     out[((size_t)m * HQ + j) * 128 + t] = __float2bfloat16_rn(acc / sum);
+}
+
+// Query-tiled causal attention for runs of consecutive tokens of one request
+// (prefill chunks): a block takes up to 64 queries of one head; each 64-key
+// tile of K and V is staged once in shared memory (FP32) and used by all of
+// them. Thread t: query t/2, dimension half t%2 (64 dims); a score is the
+// sum of the two halves. Online softmax in FP32 over key chunks of 16.
+// tiles: [n][3] = (first batch token, query count, -) ; query i of a tile is
+// batch token first + i, positions consecutive.
+__global__ void __launch_bounds__(128) k_attention_tiled(const __nv_bfloat16 *q, const __nv_bfloat16 *kc,
+                                                         const __nv_bfloat16 *vc, const int32_t *pos,
+                                                         const int32_t *req, const int32_t *btab,
+                                                         const int32_t *tiles, int max_blocks, int HQ,
+                                                         int HKV, __nv_bfloat16 *out) {
+    extern __shared__ float sm[];
+    float *Ks = sm, *Vs = sm + 64 * 128;
+    const int tile = blockIdx.x, j = blockIdx.y, t = threadIdx.x;
+    const int first = tiles[3 * tile], nq = tiles[3 * tile + 1];
+    const int qi = t >> 1, half = t & 1;
+    const int kvh = j / (HQ / HKV);
+    const int m = first + min(qi, nq - 1);
+    const int r = req[first];
+    const int p = pos[m];
+    const int p_last = pos[first + nq - 1];
+    const int32_t *bt = btab + (size_t)r * max_blocks;
+    float qv[64];
+    const __nv_bfloat16 *qr = q + ((size_t)m * HQ + j) * 128 + half * 64;
+#pragma unroll
+    for (int d = 0; d < 64; ++d) qv[d] = __bfloat162float(qr[d]) * 0.08838834764831845f;
+    float acc[64];
+#pragma unroll
+    for (int d = 0; d < 64; ++d) acc[d] = 0.0f;
+    float mx = -FLT_MAX, sum = 0.0f;
+    for (int k0 = 0; k0 <= p_last; k0 += 64) {
+        __syncthreads();
+        // stage 64 keys: 128 threads, each 64 of the 8192 values of K and of V
+        for (int e = t; e < 64 * 16; e += 128) {
+            const int kk = e >> 4, part = e & 15;  // 16 parts of 8 dims
+            const int key = k0 + kk;
+            float4 a0 = make_float4(0, 0, 0, 0), a1 = a0, b0 = a0, b1 = a0;
+            if (key <= p_last) {
+                const size_t off = (((size_t)bt[key / 16] * 16 + key % 16) * HKV + kvh) * 128 + part * 8;
+                const uint4 rk = *reinterpret_cast<const uint4 *>(kc + off);
+                const uint4 rv = *reinterpret_cast<const uint4 *>(vc + off);
+                const __nv_bfloat162 *hk = reinterpret_cast<const __nv_bfloat162 *>(&rk);
+                const __nv_bfloat162 *hv = reinterpret_cast<const __nv_bfloat162 *>(&rv);
+                float2 f;
+                f = __bfloat1622float2(hk[0]); a0.x = f.x; a0.y = f.y;
+                f = __bfloat1622float2(hk[1]); a0.z = f.x; a0.w = f.y;
+                f = __bfloat1622float2(hk[2]); a1.x = f.x; a1.y = f.y;
+                f = __bfloat1622float2(hk[3]); a1.z = f.x; a1.w = f.y;
+                f = __bfloat1622float2(hv[0]); b0.x = f.x; b0.y = f.y;
+                f = __bfloat1622float2(hv[1]); b0.z = f.x; b0.w = f.y;
+                f = __bfloat1622float2(hv[2]); b1.x = f.x; b1.y = f.y;
+                f = __bfloat1622float2(hv[3]); b1.z = f.x; b1.w = f.y;
+            }
+            float4 *kd = reinterpret_cast<float4 *>(Ks + kk * 128 + part * 8);
+            float4 *vd = reinterpret_cast<float4 *>(Vs + kk * 128 + part * 8);
+            kd[0] = a0; kd[1] = a1;
+            vd[0] = b0; vd[1] = b1;
+        }
+        __syncthreads();
+        const int kn = min(64, p_last + 1 - k0);
+        for (int c = 0; c < kn; c += 16) {
+            float sc[16];
+#pragma unroll
+            for (int z = 0; z < 16; ++z) {
+                const float *kr = Ks + (c + z) * 128 + half * 64;
+                float d0 = 0.0f;
+#pragma unroll
+                for (int d = 0; d < 64; d += 4) {
+                    const float4 kv = *reinterpret_cast<const float4 *>(kr + d);
+                    d0 = fmaf(qv[d], kv.x, d0);
+                    d0 = fmaf(qv[d + 1], kv.y, d0);
+                    d0 = fmaf(qv[d + 2], kv.z, d0);
+                    d0 = fmaf(qv[d + 3], kv.w, d0);
+                }
+                d0 += __shfl_xor_sync(0xffffffffu, d0, 1);
+                const int key = k0 + c + z;
+                sc[z] = (c + z < kn && key <= p) ? d0 : -FLT_MAX;
+            }
+            float cm = mx;
+#pragma unroll
+            for (int z = 0; z < 16; ++z) cm = fmaxf(cm, sc[z]);
+            const float scale = expf(mx - cm);
+            sum *= scale;
+#pragma unroll
+            for (int d = 0; d < 64; ++d) acc[d] *= scale;
+#pragma unroll
+            for (int z = 0; z < 16; ++z) {
+                const float pz = sc[z] == -FLT_MAX ? 0.0f : expf(sc[z] - cm);
+                sum += pz;
+                const float *vr = Vs + (c + z) * 128 + half * 64;
+#pragma unroll
+                for (int d = 0; d < 64; d += 4) {
+                    const float4 vv = *reinterpret_cast<const float4 *>(vr + d);
+                    acc[d] = fmaf(pz, vv.x, acc[d]);
+                    acc[d + 1] = fmaf(pz, vv.y, acc[d + 1]);
+                    acc[d + 2] = fmaf(pz, vv.z, acc[d + 2]);
+                    acc[d + 3] = fmaf(pz, vv.w, acc[d + 3]);
+                }
+            }
+            mx = cm;
+        }
+    }
+    if (qi < nq) {
+        __nv_bfloat16 *o = out + ((size_t)m * HQ + j) * 128 + half * 64;
+        const float inv = 1.0f / sum;
+#pragma unroll
+        for (int d = 0; d < 64; ++d) o[d] = __float2bfloat16_rn(acc[d] * inv);
+    }
 }
 
 __global__ void k_add(float *h, const float *y, size_t n) {
@@ -222,6 +334,14 @@ cloak_status serve_step_run(cloak_ctx *ctx, const cloak_serve_desc *d, const clo
     float *logits = b->out_logits ? b->out_logits : (float *)take((size_t)std::max(S, 1) * V * 4);
     __nv_bfloat16 *xs = (__nv_bfloat16 *)take((size_t)std::max(S, 1) * D * 2);
     cloak_status rc;
+    if (b->qtiles) {
+        static bool attr = false;
+        if (!attr) {
+            CLOAK_CUDA(ctx, cudaFuncSetAttribute(k_attention_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 2 * 64 * 128 * (int)sizeof(float)));
+            attr = true;
+        }
+    }
     k_embed<<<M, 256, 0, s>>>((const __nv_bfloat16 *)d->embedding, b->token_ids, D, h);
     CLOAK_LAUNCHED(ctx);
     for (int l = 0; l < sd.num_layers; ++l) {
@@ -239,9 +359,25 @@ cloak_status serve_step_run(cloak_ctx *ctx, const cloak_serve_desc *d, const clo
         k_rope_cache<<<dim3(M, HQ + HKV), 64, 0, s>>>(q, k, v, b->positions, b->req_slots, b->block_tables,
                                                       d->max_blocks, HQ, HKV, d->rope_theta, kc, vc);
         CLOAK_LAUNCHED(ctx);
-        k_attention<<<dim3(M, HQ), 128, 0, s>>>(q, kc, vc, b->positions, b->req_slots, b->block_tables,
-                                                 d->max_blocks, HQ, HKV, attn);
-        CLOAK_LAUNCHED(ctx);
+        if (b->qtiles) {
+            // prefill runs: query tiles sharing K/V tiles; decode tokens: one block each
+            if (b->num_qtiles > 0) {
+                k_attention_tiled<<<dim3(b->num_qtiles, HQ), 128, 2 * 64 * 128 * sizeof(float), s>>>(
+                    q, kc, vc, b->positions, b->req_slots, b->block_tables, b->qtiles, d->max_blocks, HQ,
+                    HKV, attn);
+                CLOAK_LAUNCHED(ctx);
+            }
+            if (b->num_single > 0) {
+                k_attention<<<dim3(b->num_single, HQ), 128, 0, s>>>(q, kc, vc, b->positions, b->req_slots,
+                                                                     b->block_tables, b->single_rows,
+                                                                     d->max_blocks, HQ, HKV, attn);
+                CLOAK_LAUNCHED(ctx);
+            }
+        } else {
+            k_attention<<<dim3(M, HQ), 128, 0, s>>>(q, kc, vc, b->positions, b->req_slots, b->block_tables,
+                                                     nullptr, d->max_blocks, HQ, HKV, attn);
+            CLOAK_LAUNCHED(ctx);
+        }
         if ((rc = linear_run(ctx, lt[3], attn, y, M, CLOAK_OUT_F32, flags, s))) return rc;
         k_add<<<nb(Mz * D), 256, 0, s>>>(h, y, Mz * D);
         CLOAK_LAUNCHED(ctx);

@@ -80,14 +80,19 @@ class ServedModel:
                                     self.v_cache.data_ptr(), kv_blocks, max_blocks, rope_theta)
 
     def step(self, token_ids, positions, req_slots, block_tables, sample_rows, out_tokens,
-             out_logits=None, uncloaked=False, stream=None):
+             out_logits=None, uncloaked=False, stream=None, qtiles=None, single_rows=None):
         """Run one forward step; all arguments are device int32 tensors
-        (out_logits: optional FP32 [num_sample, vocab])."""
+        (out_logits: optional FP32 [num_sample, vocab]; qtiles [n, 3] and
+        single_rows: optional attention work split, see cloak_serve_batch)."""
+        nq = int(qtiles.shape[0]) if qtiles is not None else 0
+        ns = int(single_rows.numel()) if single_rows is not None else 0
         b = cloak.ServeBatch(int(token_ids.numel()), int(sample_rows.numel()),
                              cloak.LINEAR_UNCLOAKED if uncloaked else 0, token_ids.data_ptr(),
                              positions.data_ptr(), req_slots.data_ptr(), block_tables.data_ptr(),
                              sample_rows.data_ptr(), out_tokens.data_ptr(),
-                             out_logits.data_ptr() if out_logits is not None else None)
+                             out_logits.data_ptr() if out_logits is not None else None, nq, ns,
+                             qtiles.data_ptr() if qtiles is not None else None,
+                             single_rows.data_ptr() if ns else None)
         cloak.cloak_serve_step(self.cm.ctx, self.desc, b, stream)
 
     def rekey(self, stream=None):
@@ -121,6 +126,9 @@ class Server:
         self.d_pos, self.d_req = torch.zeros_like(self.d_ids), torch.zeros_like(self.d_ids)
         self.d_samp, self.d_out = torch.zeros_like(self.d_ids), torch.zeros_like(self.d_ids)
         self.h_out = pin()
+        self.h_tiles = torch.zeros(3 * cap, dtype=torch.int32).pin_memory()
+        self.d_tiles = torch.zeros(3 * cap, dtype=torch.int32, device=dev)
+        self.h_single, self.d_single = pin(), torch.zeros_like(self.d_ids)
         self.stream = torch.cuda.Stream(device=dev)
         self.rekeys: List[float] = []
         self.steps = 0
@@ -147,18 +155,22 @@ class Server:
     def step_batch(self, running: List[Request]):
         """Assemble and run one step; returns per-request sampled tokens."""
         import torch
-        ids, pos, req, samp, owners = [], [], [], [], []
+        ids, pos, req, samp, owners, single, tiles = [], [], [], [], [], [], []
         budget = self.budget
         for r in running:                           # decode tokens first
             if r.prefilled == len(r.prompt) and r.out:
+                single.append(len(ids))
                 ids.append(r.out[-1]); pos.append(r.length - 1); req.append(r.slot)
                 samp.append(len(ids) - 1); owners.append(r)
                 budget -= 1
         for r in running:                           # then prefill chunks
             if r.prefilled < len(r.prompt) and budget > 0:
                 n = min(budget, len(r.prompt) - r.prefilled)
-                for i in range(r.prefilled, r.prefilled + n):
-                    ids.append(int(r.prompt[i])); pos.append(i); req.append(r.slot)
+                for t0 in range(0, n, 64):          # query tiles of the chunk
+                    tiles += [len(ids) + t0, min(64, n - t0), 0]
+                ids.extend(int(v) for v in r.prompt[r.prefilled:r.prefilled + n])
+                pos.extend(range(r.prefilled, r.prefilled + n))
+                req.extend([r.slot] * n)
                 r.prefilled += n
                 budget -= n
                 if r.prefilled == len(r.prompt):    # last prompt token samples
@@ -170,14 +182,22 @@ class Server:
         self.h_pos[:M] = torch.tensor(pos, dtype=torch.int32)
         self.h_req[:M] = torch.tensor(req, dtype=torch.int32)
         self.h_samp[:S] = torch.tensor(samp, dtype=torch.int32)
+        nt, ns = len(tiles) // 3, len(single)
+        if nt:
+            self.h_tiles[:3 * nt] = torch.tensor(tiles, dtype=torch.int32)
+        if ns:
+            self.h_single[:ns] = torch.tensor(single, dtype=torch.int32)
         with torch.cuda.stream(self.stream):
+            self.d_tiles[:3 * nt].copy_(self.h_tiles[:3 * nt], non_blocking=True)
+            self.d_single[:ns].copy_(self.h_single[:ns], non_blocking=True)
             self.d_ids[:M].copy_(self.h_ids[:M], non_blocking=True)
             self.d_pos[:M].copy_(self.h_pos[:M], non_blocking=True)
             self.d_req[:M].copy_(self.h_req[:M], non_blocking=True)
             self.d_samp[:S].copy_(self.h_samp[:S], non_blocking=True)
             self.sm.step(self.d_ids[:M], self.d_pos[:M], self.d_req[:M], self.block_tables,
                          self.d_samp[:S], self.d_out[:S], uncloaked=self.uncloaked,
-                         stream=self.stream.cuda_stream)
+                         stream=self.stream.cuda_stream,
+                         qtiles=self.d_tiles[:3 * nt].view(-1, 3), single_rows=self.d_single[:ns])
             self.h_out[:S].copy_(self.d_out[:S], non_blocking=True)
         self.stream.synchronize()
         self.steps += 1

@@ -27,9 +27,10 @@ def served(cloak_lib):
     sm.close()
 
 
-def run_steps(sm, seqs, uncloaked=False):
+def run_steps(sm, seqs, uncloaked=False, tiled=False):
     """Prefill each (slot, tokens) fully in one step, then decode 3 steps
-    feeding back greedy tokens; returns per slot the list of logits."""
+    feeding back greedy tokens; returns per slot the list of logits. With
+    `tiled`, prefill tokens use query tiles (64) and decode tokens single rows."""
     dev = "cuda"
     bt = torch.zeros((8, sm.max_blocks), dtype=torch.int32, device=dev)
     for slot, toks in seqs:
@@ -38,20 +39,28 @@ def run_steps(sm, seqs, uncloaked=False):
     logits = {slot: [] for slot, _ in seqs}
     first = True
     for step in range(4):
-        ids, pos, req, samp = [], [], [], []
+        ids, pos, req, samp, tiles, single = [], [], [], [], [], []
         for slot, toks in seqs:
             seq = state[slot]
             if first:
+                for t0 in range(0, len(seq), 64):
+                    tiles += [len(ids) + t0, min(64, len(seq) - t0), 0]
                 for i, t in enumerate(seq):
                     ids.append(t); pos.append(i); req.append(slot)
             else:
+                single.append(len(ids))
                 ids.append(seq[-1]); pos.append(len(seq) - 1); req.append(slot)
             samp.append(len(ids) - 1)
         first = False
         T = lambda a: torch.tensor(a, dtype=torch.int32, device=dev)
         out = torch.zeros(len(samp), dtype=torch.int32, device=dev)
         lg = torch.zeros((len(samp), sm.model.vocab), dtype=torch.float32, device=dev)
-        sm.step(T(ids), T(pos), T(req), bt, T(samp), out, lg, uncloaked=uncloaked)
+        if tiled:
+            qt = T(tiles).view(-1, 3) if tiles else T([]).view(0, 3)
+            sm.step(T(ids), T(pos), T(req), bt, T(samp), out, lg, uncloaked=uncloaked, qtiles=qt,
+                    single_rows=T(single))
+        else:
+            sm.step(T(ids), T(pos), T(req), bt, T(samp), out, lg, uncloaked=uncloaked)
         torch.cuda.synchronize()
         for k, (slot, _) in enumerate(seqs):
             logits[slot].append(lg[k].cpu().numpy())
@@ -59,10 +68,11 @@ def run_steps(sm, seqs, uncloaked=False):
     return logits, state
 
 
-def test_serve_step_matches_full_model_oracle(served):
+@pytest.mark.parametrize("tiled", [False, True])
+def test_serve_step_matches_full_model_oracle(served, tiled):
     m, Ws, sm = served
     toks = list(np.random.default_rng(1).integers(0, 1000, 23))
-    logits, state = run_steps(sm, [(0, toks)])
+    logits, state = run_steps(sm, [(0, toks)], tiled=tiled)
     W64 = [O.bf16_value(O.bf16_bits(w)) for w in Ws]
     emb64 = O.bf16_value(O.bf16_bits(synth.embedding_host(1000, 512)))
     seq = state[0]
@@ -75,18 +85,19 @@ def test_serve_step_matches_full_model_oracle(served):
             assert seq[23 + step] == int(np.argmax(ref[p]))
 
 
-def test_request_alone_equals_request_in_a_mix(served):
+@pytest.mark.parametrize("tiled", [False, True])
+def test_request_alone_equals_request_in_a_mix(served, tiled):
     m, Ws, sm = served
     rng = np.random.default_rng(2)
-    a = list(rng.integers(0, 1000, 17))
-    b = list(rng.integers(0, 1000, 40))
+    a = list(rng.integers(0, 1000, 77))
+    b = list(rng.integers(0, 1000, 140))
     c = list(rng.integers(0, 1000, 5))
-    alone, sa = run_steps(sm, [(0, a)])
-    mixed, sm_ = run_steps(sm, [(1, b), (0, a), (2, c)])
+    alone, sa = run_steps(sm, [(0, a)], tiled=tiled)
+    mixed, sm_ = run_steps(sm, [(1, b), (0, a), (2, c)], tiled=tiled)
     for x, y in zip(alone[0], mixed[0]):
         assert np.array_equal(x, y)
     assert sa[0] == sm_[0]
-    unc, su = run_steps(sm, [(0, a)], uncloaked=True)
+    unc, su = run_steps(sm, [(0, a)], uncloaked=True, tiled=tiled)
     for x, y in zip(alone[0], unc[0]):
         assert np.array_equal(x, y)
 
