@@ -65,7 +65,9 @@ class ServeBatch(C.Structure):
     _fields_ = [("num_tokens", C.c_int32), ("num_sample", C.c_int32), ("flags", C.c_int32),
                 ("token_ids", C.c_void_p), ("positions", C.c_void_p), ("req_slots", C.c_void_p),
                 ("block_tables", C.c_void_p), ("sample_rows", C.c_void_p),
-                ("out_tokens", C.c_void_p), ("out_logits", C.c_void_p)]
+                ("out_tokens", C.c_void_p), ("out_logits", C.c_void_p),
+                ("num_qtiles", C.c_int32), ("num_single", C.c_int32),
+                ("qtiles", C.c_void_p), ("single_rows", C.c_void_p)]
 
 
 # (name, restype, argtypes); the list is the ABI this binding expects

@@ -89,3 +89,31 @@ def test_product_path_does_not_touch_the_oracle():
                 src = open(os.path.join(dp, f)).read()
                 assert not re.search(r"(import\s+oracle|from\s+oracle|liboracle|oracle/|cloak_oracle)",
                                      src), f
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """Every descriptor struct the binding declares has the header's size and
+    field offsets (gcc compiles the header and prints them)."""
+    from paper_2606_18400_gb300 import cloak
+    structs = {"cloak_tensor_desc": cloak.TensorDesc, "cloak_group_desc": cloak.GroupDesc,
+               "cloak_model_desc": cloak.ModelDesc, "cloak_stack_desc": cloak.StackDesc,
+               "cloak_serve_desc": cloak.ServeDesc, "cloak_serve_batch": cloak.ServeBatch}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "cloak.h"', 'int main(void) {']
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f in py._fields_:
+            lines.append(f'printf("{cname} {f[0]} %zu\\n", offsetof({cname}, {f[0]}));')
+    lines += ['return 0;', '}']
+    src, exe = tmp_path / "layout.c", tmp_path / "layout"
+    src.write_text("\n".join(lines))
+    import subprocess
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    got = dict()
+    for ln in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        a, b, v = ln.split()
+        got[(a, b)] = int(v)
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == C.sizeof(py), cname
+        for f in py._fields_:
+            assert got[(cname, f[0])] == getattr(py, f[0]).offset, (cname, f[0])
