@@ -566,7 +566,8 @@ def run_serve(args):
     """Serving workload: the 32-layer cloaked BF16 model with a 32,000-token
     lm_head, Poisson arrivals, lognormal prompts clipped to [128, 4096],
     outputs uniform in [64, 1024], continuous batching admitted by free KV
-    blocks, re-key every 30 s between steps; cloaked vs uncloaked at the same
+    blocks, re-key every 30 s (concurrent: copies on a side stream, tables
+    published between steps); cloaked vs uncloaked at the same
     arrival rates. One JSON line per run of the whole sweep."""
     import torch
     from paper_2606_18400_gb300 import cloak, serve, synth
@@ -581,14 +582,18 @@ def run_serve(args):
         work = synth.requests_poisson(rate, args.serve_seconds, 32000, seed=int(rate * 10))
         row = {}
         for name, unc in (("cloaked", False), ("uncloaked", True)):
-            srv = serve.Server(sm, max_running=64, token_budget=2048, rekey_period=30.0, uncloaked=unc)
+            # the plain model has nothing to re-key
+            srv = serve.Server(sm, max_running=64, token_budget=2048, uncloaked=unc,
+                               rekey_period=None if unc else args.rekey_period,
+                               rekey_concurrent=not args.rekey_between_steps)
             done, wall = srv.run(work, max_wall=args.serve_seconds + args.drain_seconds)
             st = serve.latency_stats(done, wall)
             st["submitted"] = len(work)
             st["steps"] = srv.steps
             st["mean_step_tokens"] = float(np.mean(srv.step_tokens)) if srv.step_tokens else 0.0
             st["rekeys"] = len(srv.rekeys)
-            st["rekey_ms"] = [round(x * 1e3, 2) for x in srv.rekeys]
+            st["rekey_detail"] = [{k: (round(v, 3) if isinstance(v, float) else v) for k, v in r.items()}
+                                  for r in srv.rekeys]
             row[name] = st
         results[str(rate)] = row
     clk = clocks.stop()
@@ -601,7 +606,10 @@ def run_serve(args):
             "config": {"workload": f"Poisson {args.rates} req/s for {args.serve_seconds} s each (+ up to "
                                    f"{args.drain_seconds} s drain), prompts lognormal median 1024 clipped "
                                    f"[128, 4096], outputs U[64, 1024], 32 layers + vocab 32000, "
-                                   f"KV pool {args.kv_blocks} blocks of 16 tokens, re-key every 30 s"},
+                                   f"KV pool {args.kv_blocks} blocks of 16 tokens, re-key every "
+                                   f"{args.rekey_period:g} s "
+                                   f"({'between steps' if args.rekey_between_steps else 'concurrent, side stream'})"
+                                   f" on the cloaked arm"},
             "sweep": results, "clocks": clk}
     print(json.dumps(line), flush=True)
 
@@ -658,6 +666,9 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=30.0)
     ap.add_argument("--drain-seconds", type=float, default=30.0)
     ap.add_argument("--kv-blocks", type=int, default=7000)
+    ap.add_argument("--rekey-period", type=float, default=30.0)
+    ap.add_argument("--rekey-between-steps", action="store_true",
+                    help="serving: re-key between two steps instead of concurrently")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

@@ -291,6 +291,27 @@ CLOAK_API cloak_status cloak_serve_step(cloak_ctx *ctx, const cloak_serve_desc *
  * on the same stream or with events. */
 CLOAK_API cloak_status cloak_rekey(cloak_ctx *ctx, uint64_t key, uint32_t new_epoch, void *stream);
 
+/* Concurrent re-key: the same moves as cloak_rekey, made while the model
+ * keeps serving. The remap of Section 4.2 pauses execution at a sync point;
+ * here no step waits for the copy. cloak_rekey_begin draws the page map of (key,
+ * new_epoch), plans the moves (blocking the calling thread on `side_stream`
+ * only) and starts the first wave of page copies on `side_stream`. Every wave
+ * writes only pages that no published gather-table entry points at. Then, at
+ * each step boundary of the serving stream, cloak_rekey_advance checks
+ * (without blocking) whether the wave in flight has landed; if so it enqueues
+ * on `serve_stream` the table update that points the moved tiles at their
+ * new slots, and starts the next wave on `side_stream` after that update.
+ * Until *done = 1 all calls that read the model (linear, stack, serve step,
+ * unshuffle) must be ordered on `serve_stream`, and keygen, shuffle and
+ * cloak_rekey return CLOAK_E_STATE. At *done = 1 (the last update enqueued)
+ * the arena and tables are those of keygen(key, new_epoch) + shuffle.
+ * Errors: CLOAK_E_STATE (no job / a job already running), CLOAK_E_INVAL
+ * (wrong key, the two streams equal, null `done`). */
+CLOAK_API cloak_status cloak_rekey_begin(cloak_ctx *ctx, uint64_t key, uint32_t new_epoch,
+                                         void *side_stream);
+CLOAK_API cloak_status cloak_rekey_advance(cloak_ctx *ctx, void *serve_stream, void *side_stream,
+                                           int32_t *done);
+
 /* Status recorded by device code (bounded waits, bounds checks) since the
  * last call; reading it synchronises the device and clears it. */
 CLOAK_API cloak_status cloak_device_status(cloak_ctx *ctx);

@@ -90,6 +90,8 @@ SIGNATURES = [
     ("cloak_stack_decode", _i32, [_vp, C.POINTER(StackDesc), _vp, _i32, _i32, _vp]),
     ("cloak_serve_step", _i32, [_vp, C.POINTER(ServeDesc), C.POINTER(ServeBatch), _vp]),
     ("cloak_rekey", _i32, [_vp, _u64, _u32, _vp]),
+    ("cloak_rekey_begin", _i32, [_vp, _u64, _u32, _vp]),
+    ("cloak_rekey_advance", _i32, [_vp, _vp, _vp, C.POINTER(_i32)]),
     ("cloak_device_status", _i32, [_vp]),
     ("cloak_last_error", C.c_char_p, [_vp]),
     ("cloak_launch_count", _i64, [_vp]),
@@ -222,6 +224,18 @@ def cloak_serve_step(ctx, desc: ServeDesc, batch: ServeBatch, stream=None):
 
 def cloak_rekey(ctx, key: int, new_epoch: int, stream=None):
     _check("cloak_rekey", load().cloak_rekey(ctx, key & (2**64 - 1), new_epoch, _stream(stream)), ctx)
+
+
+def cloak_rekey_begin(ctx, key: int, new_epoch: int, side_stream):
+    _check("cloak_rekey_begin", load().cloak_rekey_begin(ctx, key & (2**64 - 1), new_epoch,
+                                                         _stream(side_stream)), ctx)
+
+
+def cloak_rekey_advance(ctx, serve_stream, side_stream) -> bool:
+    done = C.c_int32(0)
+    _check("cloak_rekey_advance", load().cloak_rekey_advance(ctx, _stream(serve_stream),
+                                                             _stream(side_stream), C.byref(done)), ctx)
+    return bool(done.value)
 
 
 def cloak_device_status(ctx) -> int:
@@ -367,6 +381,12 @@ class CloakModel:
 
     def rekey(self, key, new_epoch, stream=None):
         cloak_rekey(self.ctx, key, new_epoch, stream)
+
+    def rekey_begin(self, key, new_epoch, side_stream):
+        cloak_rekey_begin(self.ctx, key, new_epoch, side_stream)
+
+    def rekey_advance(self, serve_stream, side_stream) -> bool:
+        return cloak_rekey_advance(self.ctx, serve_stream, side_stream)
 
     def arena_bytes(self, which=0):
         """The arena (0) or the twin (1) as a uint8 device view (no copy)."""

@@ -7,7 +7,7 @@ import pytest
 import torch
 
 import oracle as O
-from paper_2606_18400_gb300 import serve, synth
+from paper_2606_18400_gb300 import cloak, serve, synth
 
 pytestmark = pytest.mark.gpu
 
@@ -108,9 +108,10 @@ def test_server_serves_a_workload_with_rekeys(cloak_lib):
     work = [(0.01 * i, np.random.default_rng(10 + i).integers(0, 1000, 20 + 7 * i).astype(np.int32), 4 + i % 5)
             for i in range(10)]
     outs = []
-    for period in (None, 0.02):
+    for period, conc in ((None, True), (0.02, True), (0.02, False)):
         sm = serve.ServedModel(m, kv_blocks=128, max_blocks=16, weights=Ws)
-        srv = serve.Server(sm, max_running=4, token_budget=64, rekey_period=period)
+        srv = serve.Server(sm, max_running=4, token_budget=64, rekey_period=period,
+                           rekey_concurrent=conc)
         done, wall = srv.run(work)
         assert len(done) == 10 and all(len(r.out) == r.max_new for r in done)
         st = serve.latency_stats(done, wall)
@@ -118,6 +119,11 @@ def test_server_serves_a_workload_with_rekeys(cloak_lib):
         outs.append({r.rid: r.out for r in done})
         if period:
             assert len(srv.rekeys) >= 1
+            assert all(r["mode"] == ("concurrent" if conc else "between_steps") for r in srv.rekeys)
+            # every re-key ran to its end: the tables are those of the last epoch
+            tb = O.keygen(O.OracleModel(m), sm.key, sm.epoch)
+            assert np.array_equal(sm.cm.table(cloak.TAB_TILE_SLOT), tb.tile_slot)
         assert sm.cm.device_status() == 0
         sm.close()
-    assert outs[0] == outs[1]  # continuous batching and re-keys do not change results
+    # continuous batching and re-keys (between steps or concurrent) do not change results
+    assert outs[0] == outs[1] == outs[2]
