@@ -81,69 +81,136 @@ __global__ void k_rope_cache(__nv_bfloat16 *q, const __nv_bfloat16 *k, const __n
     }
 }
 
-// Causal attention of one query (token m, head j) over positions 0..pos[m]
-// of its request: 128 threads; keys in chunks of 128 (one per thread), online
-// softmax in FP32; each thread accumulates one output dimension.
-__global__ void __launch_bounds__(128) k_attention(const __nv_bfloat16 *q, const __nv_bfloat16 *kc,
-                                                   const __nv_bfloat16 *vc, const int32_t *pos,
-                                                   const int32_t *req, const int32_t *btab,
-                                                   const int32_t *rows, int max_blocks, int HQ, int HKV,
-                                                   __nv_bfloat16 *out) {
-    const int m = rows ? rows[blockIdx.x] : (int)blockIdx.x, j = blockIdx.y, t = threadIdx.x;
-    const int kvh = j / (HQ / HKV);
+// Causal attention of single queries (decode tokens), split over the keys:
+// block (split, row, head) takes keys [256 split, 256 split + 256) of token
+// m = rows[row]; each of its 4 warps 64 of them, 8 at a time. A lane holds 4
+// of the 128 dimensions: K and V rows are read as 256-byte coalesced warp
+// loads, 16 of them in flight per lane; scores are warp sums. Online softmax
+// in FP32 per warp, merged across the warps in shared memory. A token with
+// one split writes its output; otherwise the block writes (max, sum,
+// acc[128]) and k_attn_combine merges the splits in order. The split depends
+// only on the token's own position, so the result does not depend on the
+// batch.
+constexpr int ATT_SPLIT = 256;
+constexpr int ATT_PART = 132;  // floats per partial: max, sum, pad, acc[128]
+
+__global__ void __launch_bounds__(128) k_attn_decode(const __nv_bfloat16 *q, const __nv_bfloat16 *kc,
+                                                     const __nv_bfloat16 *vc, const int32_t *pos,
+                                                     const int32_t *req, const int32_t *btab,
+                                                     const int32_t *rows, int max_blocks, int HQ,
+                                                     int HKV, int max_splits, float *part,
+                                                     __nv_bfloat16 *out) {
+    const int sp = blockIdx.x, r = blockIdx.y, j = blockIdx.z;
+    const int m = rows ? rows[r] : r;
     const int n = pos[m] + 1;
+    const int nsplit = (n + ATT_SPLIT - 1) / ATT_SPLIT;
+    if (sp >= nsplit) return;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int kvh = j / (HQ / HKV);
     const int32_t *bt = btab + (size_t)req[m] * max_blocks;
-    __shared__ float qs[128];
-    __shared__ float ps[128];
-    __shared__ float red[4];
-    qs[t] = __bfloat162float(q[((size_t)m * HQ + j) * 128 + t]) * 0.08838834764831845f;  // 1/sqrt(128)
-    __syncthreads();
-    float mx = -FLT_MAX, sum = 0.0f, acc = 0.0f;
-    for (int c0 = 0; c0 < n; c0 += 128) {
-        const int key = c0 + t;
-        float s = -FLT_MAX;
-        if (key < n) {
-            const __nv_bfloat16 *kr = kc + (((size_t)bt[key / 16] * 16 + key % 16) * HKV + kvh) * 128;
-            float d = 0.0f;
-            for (int e = 0; e < 128; e += 8) {
-                const uint4 raw = *reinterpret_cast<const uint4 *>(kr + e);
-                const __nv_bfloat162 *h2 = reinterpret_cast<const __nv_bfloat162 *>(&raw);
-#pragma unroll
-                for (int z = 0; z < 4; ++z) {
-                    const float2 f = __bfloat1622float2(h2[z]);
-                    d = fmaf(qs[e + 2 * z], f.x, d);
-                    d = fmaf(qs[e + 2 * z + 1], f.y, d);
-                }
-            }
-            s = d;
-        }
-        // chunk max
-        float cm = s;
-        for (int o = 16; o; o >>= 1) cm = fmaxf(cm, __shfl_xor_sync(0xffffffffu, cm, o));
-        if ((t & 31) == 0) red[t >> 5] = cm;
-        __syncthreads();
-        cm = fmaxf(fmaxf(red[0], red[1]), fmaxf(red[2], red[3]));
-        __syncthreads();
-        const float nmx = fmaxf(mx, cm);
-        const float scale = expf(mx - nmx);
-        const float p = key < n ? expf(s - nmx) : 0.0f;
-        ps[t] = p;
-        float cs = p;
-        for (int o = 16; o; o >>= 1) cs += __shfl_xor_sync(0xffffffffu, cs, o);
-        if ((t & 31) == 0) red[t >> 5] = cs;
-        __syncthreads();
-        sum = sum * scale + red[0] + red[1] + red[2] + red[3];
-        acc *= scale;
-        const int kn = min(128, n - c0);
-        for (int z = 0; z < kn; ++z) {
-            const int key2 = c0 + z;
-            const __nv_bfloat16 *vr = vc + (((size_t)bt[key2 / 16] * 16 + key2 % 16) * HKV + kvh) * 128;
-            acc = fmaf(ps[z], __bfloat162float(vr[t]), acc);
-        }
-        mx = nmx;
-        __syncthreads();
+    float qd[4];
+    {
+        const uint2 raw = *reinterpret_cast<const uint2 *>(q + ((size_t)m * HQ + j) * 128 + 4 * lane);
+        const __nv_bfloat162 *h2 = reinterpret_cast<const __nv_bfloat162 *>(&raw);
+        const float2 a = __bfloat1622float2(h2[0]), b = __bfloat1622float2(h2[1]);
+        const float sc = 0.08838834764831845f;  // 1/sqrt(128)
+        qd[0] = a.x * sc; qd[1] = a.y * sc; qd[2] = b.x * sc; qd[3] = b.y * sc;
     }
-    out[((size_t)m * HQ + j) * 128 + t] = __float2bfloat16_rn(acc / sum);
+    const int k_begin = sp * ATT_SPLIT + w * (ATT_SPLIT / 4);
+    const int k_end = min(n, k_begin + ATT_SPLIT / 4);
+    float mx = -FLT_MAX, sum = 0.0f, acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    for (int kb = k_begin; kb < k_end; kb += 8) {
+        uint2 kr[8], vr[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int key = min(kb + i, k_end - 1);
+            const size_t off = (((size_t)bt[key >> 4] * 16 + (key & 15)) * HKV + kvh) * 128 + 4 * lane;
+            kr[i] = *reinterpret_cast<const uint2 *>(kc + off);
+            vr[i] = *reinterpret_cast<const uint2 *>(vc + off);
+        }
+        float s[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const __nv_bfloat162 *h2 = reinterpret_cast<const __nv_bfloat162 *>(&kr[i]);
+            const float2 a = __bfloat1622float2(h2[0]), b = __bfloat1622float2(h2[1]);
+            s[i] = fmaf(qd[0], a.x, fmaf(qd[1], a.y, fmaf(qd[2], b.x, qd[3] * b.y)));
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) s[i] += __shfl_xor_sync(0xffffffffu, s[i], o);
+        }
+        float cm = mx;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            if (kb + i >= k_end) s[i] = -FLT_MAX;
+            cm = fmaxf(cm, s[i]);
+        }
+        const float scale = expf(mx - cm);
+        sum *= scale;
+#pragma unroll
+        for (int d = 0; d < 4; ++d) acc[d] *= scale;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const float p = kb + i < k_end ? expf(s[i] - cm) : 0.0f;
+            sum += p;
+            const __nv_bfloat162 *h2 = reinterpret_cast<const __nv_bfloat162 *>(&vr[i]);
+            const float2 a = __bfloat1622float2(h2[0]), b = __bfloat1622float2(h2[1]);
+            acc[0] = fmaf(p, a.x, acc[0]);
+            acc[1] = fmaf(p, a.y, acc[1]);
+            acc[2] = fmaf(p, b.x, acc[2]);
+            acc[3] = fmaf(p, b.y, acc[3]);
+        }
+        mx = cm;
+    }
+    // merge the four warps
+    __shared__ float wm[4], wl[4];
+    __shared__ float wa[4][128];
+    if (lane == 0) { wm[w] = mx; wl[w] = sum; }
+#pragma unroll
+    for (int d = 0; d < 4; ++d) wa[w][4 * lane + d] = acc[d];
+    __syncthreads();
+    const int t = threadIdx.x;
+    float M = -FLT_MAX;
+#pragma unroll
+    for (int v = 0; v < 4; ++v)
+        if (wl[v] > 0.0f) M = fmaxf(M, wm[v]);
+    float L = 0.0f, A = 0.0f;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        if (wl[v] > 0.0f) {
+            const float e = expf(wm[v] - M);
+            L = fmaf(wl[v], e, L);
+            A = fmaf(wa[v][t], e, A);
+        }
+    }
+    if (nsplit == 1) {
+        out[((size_t)m * HQ + j) * 128 + t] = __float2bfloat16_rn(A / L);
+        return;
+    }
+    float *pp = part + (((size_t)r * HQ + j) * max_splits + sp) * ATT_PART;
+    if (t == 0) { pp[0] = M; pp[1] = L; }
+    pp[4 + t] = A;
+}
+
+// Merge the splits of tokens with more than one, in split order.
+__global__ void __launch_bounds__(128) k_attn_combine(const int32_t *pos, const int32_t *rows, int HQ,
+                                                      int max_splits, const float *part,
+                                                      __nv_bfloat16 *out) {
+    const int r = blockIdx.x, j = blockIdx.y, t = threadIdx.x;
+    const int m = rows ? rows[r] : r;
+    const int nsplit = (pos[m] + ATT_SPLIT) / ATT_SPLIT;
+    if (nsplit == 1) return;
+    const float *pp = part + ((size_t)r * HQ + j) * max_splits * ATT_PART;
+    float M = -FLT_MAX;
+    for (int sp = 0; sp < nsplit; ++sp) M = fmaxf(M, pp[sp * ATT_PART]);
+    float L = 0.0f, A = 0.0f;
+    for (int sp = 0; sp < nsplit; ++sp) {
+        const float e = expf(pp[sp * ATT_PART] - M);
+        L = fmaf(pp[sp * ATT_PART + 1], e, L);
+        A = fmaf(pp[sp * ATT_PART + 4 + t], e, A);
+    }
+    out[((size_t)m * HQ + j) * 128 + t] = __float2bfloat16_rn(A / L);
 }
 
 // Query-tiled causal attention for runs of consecutive tokens of one request
@@ -310,9 +377,17 @@ cloak_status serve_step_run(cloak_ctx *ctx, const cloak_serve_desc *d, const clo
     // workspace: h, y (fp32 [M, max(D, F)]), g, u (fp32 [M, F]), x, attn, q, k, v, act (bf16), logits
     const size_t Mz = (size_t)M;
     auto r256 = [](size_t n) { return (n + 255) & ~(size_t)255; };
+    // single-query attention: every token without a work split, split over the keys
+    const int n_single = b->qtiles ? b->num_single : M;
+    const int32_t *single = b->qtiles ? b->single_rows : nullptr;
+    if (n_single < 0 || n_single > M || (b->qtiles && (b->num_qtiles < 0 || (n_single && !single))))
+        return CLOAK_E_INVAL;
+    const int max_splits = (d->max_blocks * 16 + ATT_SPLIT - 1) / ATT_SPLIT;
+    const size_t part_bytes = (size_t)std::max(n_single, 1) * HQ * max_splits * ATT_PART * 4;
     const size_t need = r256(Mz * D * 4) + r256(Mz * D * 4) + 2 * r256(Mz * F * 4) + r256(Mz * D * 2) +
                         r256(Mz * QD * 2) * 2 + 2 * r256(Mz * KD * 2) + r256(Mz * F * 2) +
-                        r256((size_t)std::max(S, 1) * V * 4) + r256((size_t)std::max(S, 1) * D * 2);
+                        r256((size_t)std::max(S, 1) * V * 4) + r256((size_t)std::max(S, 1) * D * 2) +
+                        r256(part_bytes);
     if (need > ctx->serve_ws_cap) {
         if (ctx->d_serve_ws) CLOAK_CUDA(ctx, cudaFree(ctx->d_serve_ws));
         ctx->d_serve_ws = nullptr;
@@ -333,6 +408,7 @@ cloak_status serve_step_run(cloak_ctx *ctx, const cloak_serve_desc *d, const clo
     __nv_bfloat16 *act = (__nv_bfloat16 *)take(Mz * F * 2);
     float *logits = b->out_logits ? b->out_logits : (float *)take((size_t)std::max(S, 1) * V * 4);
     __nv_bfloat16 *xs = (__nv_bfloat16 *)take((size_t)std::max(S, 1) * D * 2);
+    float *apart = (float *)take(part_bytes);
     cloak_status rc;
     if (b->qtiles) {
         static bool attr = false;
@@ -359,23 +435,21 @@ cloak_status serve_step_run(cloak_ctx *ctx, const cloak_serve_desc *d, const clo
         k_rope_cache<<<dim3(M, HQ + HKV), 64, 0, s>>>(q, k, v, b->positions, b->req_slots, b->block_tables,
                                                       d->max_blocks, HQ, HKV, d->rope_theta, kc, vc);
         CLOAK_LAUNCHED(ctx);
-        if (b->qtiles) {
-            // prefill runs: query tiles sharing K/V tiles; decode tokens: one block each
-            if (b->num_qtiles > 0) {
-                k_attention_tiled<<<dim3(b->num_qtiles, HQ), 128, 2 * 64 * 128 * sizeof(float), s>>>(
-                    q, kc, vc, b->positions, b->req_slots, b->block_tables, b->qtiles, d->max_blocks, HQ,
-                    HKV, attn);
-                CLOAK_LAUNCHED(ctx);
-            }
-            if (b->num_single > 0) {
-                k_attention<<<dim3(b->num_single, HQ), 128, 0, s>>>(q, kc, vc, b->positions, b->req_slots,
-                                                                     b->block_tables, b->single_rows,
-                                                                     d->max_blocks, HQ, HKV, attn);
-                CLOAK_LAUNCHED(ctx);
-            }
-        } else {
-            k_attention<<<dim3(M, HQ), 128, 0, s>>>(q, kc, vc, b->positions, b->req_slots, b->block_tables,
-                                                     nullptr, d->max_blocks, HQ, HKV, attn);
+        if (b->qtiles && b->num_qtiles > 0) {
+            // prefill runs: query tiles sharing staged K/V tiles
+            k_attention_tiled<<<dim3(b->num_qtiles, HQ), 128, 2 * 64 * 128 * sizeof(float), s>>>(
+                q, kc, vc, b->positions, b->req_slots, b->block_tables, b->qtiles, d->max_blocks, HQ,
+                HKV, attn);
+            CLOAK_LAUNCHED(ctx);
+        }
+        if (n_single > 0) {
+            // single queries (all tokens without a work split): split over the keys
+            k_attn_decode<<<dim3(max_splits, n_single, HQ), 128, 0, s>>>(
+                q, kc, vc, b->positions, b->req_slots, b->block_tables, single, d->max_blocks, HQ, HKV,
+                max_splits, apart, attn);
+            CLOAK_LAUNCHED(ctx);
+            k_attn_combine<<<dim3(n_single, HQ), 128, 0, s>>>(b->positions, single, HQ, max_splits, apart,
+                                                              attn);
             CLOAK_LAUNCHED(ctx);
         }
         if ((rc = linear_run(ctx, lt[3], attn, y, M, CLOAK_OUT_F32, flags, s))) return rc;

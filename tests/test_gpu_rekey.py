@@ -109,7 +109,10 @@ def test_concurrent_rekey_serves_throughout_and_ends_at_fresh_shuffle(cloak_lib,
     m = mk()
     key = 0x5EED
     cm, om, tb0, arena0, scales, Ws = place_both(cloak_lib, m, key=key, epoch=0, twin=False)
-    xs = {t: x_device(m, synth.activations_host(4, tt.k, seed=40 + t)) for t, tt in enumerate(m.tensors)}
+    # (an FP32 model with 128x128 tiles has no linear kernel: layout only)
+    runs = m.dtype != synth.DT_F32 or m.tile_r == 64
+    xs = {t: x_device(m, synth.activations_host(4, tt.k, seed=40 + t))
+          for t, tt in enumerate(m.tensors) if runs}
     y_ref = {t: cm.linear(t, xs[t], out_dtype=cloak_lib.OUT_F32).cpu() for t in xs}
     for e in (1, 2):
         steps = _concurrent_rekey(cloak_lib, cm, m, key, e, xs, y_ref)
