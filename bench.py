@@ -211,7 +211,14 @@ def traffic_record(kernel_src):
     return rec.get("dram_bytes_per_step") if rec.get("source_sha") == h else None
 
 
-def bench_extras(cloak, synth, torch, dev, stream, key, steps):
+def tuned_shape(r):
+    """The autotuner's choice, as reported in the JSON line."""
+    return {"chunk": r["chunk"], "stages": r["stages"], "grid": r["grid"],
+            "tuned_us": round(r["us"], 2), "default_us": round(r["default_us"], 2),
+            "candidates": r["candidates"]}
+
+
+def bench_extras(cloak, synth, torch, dev, stream, key, steps, tune=True):
     """Other rows of the hot path, each on its own context: BF16 prefill of the
     7B-class layer (M = 512, 2048), the FP8 GQA layer (decode M = 1 and
     prefill M = 2048), and the in-place re-key of the 32-layer 12.95 GB stack."""
@@ -244,6 +251,9 @@ def bench_extras(cloak, synth, torch, dev, stream, key, steps):
               for i, t in enumerate(model.tensors)]
         ys = [torch.empty((M, t.n), dtype=torch.bfloat16, device="cuda") for t in model.tensors]
         res = {}
+        if tune:
+            res["launch_shape"] = tuned_shape(cm.autotune(list(range(T)), xs, ys, out_dtype=cloak.OUT_BF16,
+                                                          stream=stream.cuda_stream))
         for name, flags in (("cloaked", 0), ("uncloaked", cloak.LINEAR_UNCLOAKED)):
             def fn(flags=flags):
                 cloak.cloak_linear_batch(cm.ctx, list(range(T)), [x.data_ptr() for x in xs],
@@ -266,7 +276,8 @@ def bench_extras(cloak, synth, torch, dev, stream, key, steps):
         r = layer_run(cm, model, M, 300)
         pre[str(M)] = {"cloaked_tflops": round(flops1 * M / (r["cloaked"] / 1e3) / 1e12, 1),
                        "uncloaked_tflops": round(flops1 * M / (r["uncloaked"] / 1e3) / 1e12, 1),
-                       "cloaked_ms": round(r["cloaked"], 4), "uncloaked_ms": round(r["uncloaked"], 4)}
+                       "cloaked_ms": round(r["cloaked"], 4), "uncloaked_ms": round(r["uncloaked"], 4),
+                       "launch_shape": r.get("launch_shape")}
     out["prefill_bf16_llama7b_layer"] = pre
     cm.close()
     torch.cuda.empty_cache()
@@ -283,10 +294,12 @@ def bench_extras(cloak, synth, torch, dev, stream, key, steps):
     b1 = wbytes + 4 * cm.G + sum(2 * t.k + 2 * t.n + 4 * t.n for t in model.tensors)  # x, y, row scales
     f8["decode_M1"] = {"cloaked_gbs": round(b1 / (r["cloaked"] / 1e3) / 1e9, 1),
                        "uncloaked_gbs": round(b1 / (r["uncloaked"] / 1e3) / 1e9, 1),
-                       "cloaked_us": round(r["cloaked"] * 1e3, 2), "weight_bytes": wbytes}
+                       "cloaked_us": round(r["cloaked"] * 1e3, 2), "weight_bytes": wbytes,
+                       "launch_shape": r.get("launch_shape")}
     r = layer_run(cm, model, 2048, 500)
     f8["prefill_M2048"] = {"cloaked_tflops": round(2 * wbytes * 2048 / (r["cloaked"] / 1e3) / 1e12, 1),
-                           "uncloaked_tflops": round(2 * wbytes * 2048 / (r["uncloaked"] / 1e3) / 1e12, 1)}
+                           "uncloaked_tflops": round(2 * wbytes * 2048 / (r["uncloaked"] / 1e3) / 1e12, 1),
+                           "launch_shape": r.get("launch_shape")}
     out["fp8_gqa3584_layer"] = f8
     cm.close()
     torch.cuda.empty_cache()
@@ -425,6 +438,10 @@ def run_cloak(args):
     clocks = ClockSampler(dev)
     M = args.M
     xs, ys = make_io(M)
+    shape = None
+    if not args.no_tune:  # launch shape from the autotuner (measured here, on this GPU)
+        shape = tuned_shape(cm.autotune(list(range(T)), xs, ys, out_dtype=cloak.OUT_BF16,
+                                        stream=stream.cuda_stream))
     g_cl, launches_per_step = graph_of(xs, ys, M, False)
     g_un, _ = graph_of(xs, ys, M, True)
     ms = time_graph(g_cl, args.steps, args.warmup)
@@ -471,6 +488,10 @@ def run_cloak(args):
     sweep = {}
     for Ms in (1, 8, 32, 64):
         xs2, ys2 = make_io(Ms)
+        sh = None
+        if not args.no_tune:
+            sh = tuned_shape(cm.autotune(list(range(T)), xs2, ys2, out_dtype=cloak.OUT_BF16,
+                                         stream=stream.cuda_stream))
         gc, _ = graph_of(xs2, ys2, Ms, False)
         gu, _ = graph_of(xs2, ys2, Ms, True)
         mc = time_graph(gc, max(20, args.steps), 3)
@@ -478,7 +499,8 @@ def run_cloak(args):
         Bs = step_bytes(model, Ms)
         sweep[str(Ms)] = {"cloaked_gbs": round(Bs / (mc / 1e3) / 1e9, 1),
                           "uncloaked_gbs": round(Bs / (mu / 1e3) / 1e9, 1),
-                          "cloaked_us": round(mc * 1e3, 2), "uncloaked_us": round(mu * 1e3, 2)}
+                          "cloaked_us": round(mc * 1e3, 2), "uncloaked_us": round(mu * 1e3, 2),
+                          "launch_shape": sh}
         del gc, gu, xs2, ys2
 
     # end to end through the C ABI with host buffers (copies inside the timing)
@@ -515,7 +537,7 @@ def run_cloak(args):
     status = cm.device_status()
     cm.close()
     extras = None if args.no_extras else bench_extras(cloak, synth, torch, dev, stream, KEY + rank,
-                                                      args.steps)
+                                                      args.steps, tune=not args.no_tune)
     clk = clocks.stop()
 
     if rank == 0:
@@ -534,6 +556,7 @@ def run_cloak(args):
             "config": {"workload": WORKLOAD, "batch": M, "weight_bytes": sum(t.n * t.k * 2 for t in model.tensors),
                        "bytes_per_step": B, "tiles": cm.G, "pages": cm.NP, "spare_pages": model.spare_pages,
                        "launch": "CUDA graph of one grouped launch (7 linears) per step",
+                       "launch_shape": shape,
                        "l2": "inputs larger than L2: 404.75 MB of weights per step vs 129 MB L2"},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
                          "unit": "GB/s", "frac": round(achieved / hbm, 4),
@@ -667,6 +690,8 @@ def main():
     ap.add_argument("--drain-seconds", type=float, default=30.0)
     ap.add_argument("--kv-blocks", type=int, default=7000)
     ap.add_argument("--rekey-period", type=float, default=30.0)
+    ap.add_argument("--no-tune", action="store_true",
+                    help="default launch shapes (skip the autotuner)")
     ap.add_argument("--rekey-between-steps", action="store_true",
                     help="serving: re-key between two steps instead of concurrently")
     args = ap.parse_args()

@@ -282,6 +282,39 @@ typedef struct {
 CLOAK_API cloak_status cloak_serve_step(cloak_ctx *ctx, const cloak_serve_desc *desc,
                                         const cloak_serve_batch *batch, void *stream);
 
+/* Launch-shape autotuner of the tensor-core linear (BF16 / E4M3 models).
+ * Times, with CUDA events on `stream`, the candidate launch shapes of
+ * cloak_linear_batch(ctx, n, tensors, x_dev, y_dev, M, out_dtype, 0): the
+ * activation chunk (UMMA N of one launch), the depth of the TMA gather ring
+ * and the CTA count of the stream-K split; keeps the fastest (or the
+ * default, if none beats it) for (weight dtype, the n weight shapes, the M
+ * bucket), and reports it in `out`. Later linear calls with that key use it,
+ * cloaked or uncloaked and for either output type alike (the same summation
+ * order); the serving step keeps the default CTA count. Runs the real computation: the y
+ * buffers are overwritten. Blocks until the measurements are done.
+ * CLOAK_E_UNSUPPORTED for FP32 models. */
+typedef struct {
+    int32_t chunk;        /* tokens per launch; 0: the whole batch (up to 256)  */
+    int32_t stages;       /* TMA ring depth                                     */
+    int32_t grid;         /* CTAs of the stream-K split; 0: one per SM          */
+    float us;             /* time of the chosen shape, microseconds             */
+    float default_us;     /* time of the default shape                          */
+    int32_t candidates;   /* shapes measured                                    */
+} cloak_tune_result;
+CLOAK_API cloak_status cloak_autotune(cloak_ctx *ctx, int32_t n, const int32_t *tensors,
+                                      const void *const *x_dev, void *const *y_dev, int32_t M,
+                                      int32_t out_dtype, void *stream, cloak_tune_result *out);
+/* Write the tuned shapes as JSON lines ({"chunk", "stages", "grid", "us",
+ * "key"}) / read such a file, adding its entries (count in *entries). A key
+ * reads "<bf16|e4m3> m<bucket> <N>x<K> ..." (the bucket is the UMMA N for
+ * M <= 256: 16, 32, 64, 128 or 256; above, M rounded up to 256; then each
+ * weight's shape in call order).
+ * CLOAK_E_INVAL if the file cannot be opened or a line does not parse. */
+CLOAK_API cloak_status cloak_tune_save(const cloak_ctx *ctx, const char *path);
+CLOAK_API cloak_status cloak_tune_load(cloak_ctx *ctx, const char *path, int32_t *entries);
+/* Forget every tuned shape (back to the defaults). */
+CLOAK_API cloak_status cloak_tune_clear(cloak_ctx *ctx);
+
 /* Re-key (periodic re-randomisation, Section 4.2 and Figure 7): draw the page
  * map of (key, new_epoch) and move every placed page to its new physical page
  * in place, through a small staging pool, so the arena ends bit-identical to

@@ -61,6 +61,11 @@ class ServeDesc(C.Structure):
                 ("num_blocks", C.c_int32), ("max_blocks", C.c_int32), ("rope_theta", C.c_float)]
 
 
+class TuneResult(C.Structure):
+    _fields_ = [("chunk", C.c_int32), ("stages", C.c_int32), ("grid", C.c_int32), ("us", C.c_float),
+                ("default_us", C.c_float), ("candidates", C.c_int32)]
+
+
 class ServeBatch(C.Structure):
     _fields_ = [("num_tokens", C.c_int32), ("num_sample", C.c_int32), ("flags", C.c_int32),
                 ("token_ids", C.c_void_p), ("positions", C.c_void_p), ("req_slots", C.c_void_p),
@@ -91,6 +96,11 @@ SIGNATURES = [
     ("cloak_serve_step", _i32, [_vp, C.POINTER(ServeDesc), C.POINTER(ServeBatch), _vp]),
     ("cloak_rekey", _i32, [_vp, _u64, _u32, _vp]),
     ("cloak_rekey_begin", _i32, [_vp, _u64, _u32, _vp]),
+    ("cloak_autotune", _i32, [_vp, _i32, C.POINTER(_i32), C.POINTER(_vp), C.POINTER(_vp), _i32, _i32, _vp,
+                              C.POINTER(TuneResult)]),
+    ("cloak_tune_save", _i32, [_vp, C.c_char_p]),
+    ("cloak_tune_load", _i32, [_vp, C.c_char_p, C.POINTER(_i32)]),
+    ("cloak_tune_clear", _i32, [_vp]),
     ("cloak_rekey_advance", _i32, [_vp, _vp, _vp, C.POINTER(_i32)]),
     ("cloak_device_status", _i32, [_vp]),
     ("cloak_last_error", C.c_char_p, [_vp]),
@@ -224,6 +234,31 @@ def cloak_serve_step(ctx, desc: ServeDesc, batch: ServeBatch, stream=None):
 
 def cloak_rekey(ctx, key: int, new_epoch: int, stream=None):
     _check("cloak_rekey", load().cloak_rekey(ctx, key & (2**64 - 1), new_epoch, _stream(stream)), ctx)
+
+
+def cloak_autotune(ctx, tensors, x_devs, y_devs, M: int, out_dtype: int, stream=None) -> dict:
+    n = len(tensors)
+    ta = (C.c_int32 * n)(*tensors)
+    xa = (C.c_void_p * n)(*x_devs)
+    ya = (C.c_void_p * n)(*y_devs)
+    r = TuneResult()
+    _check("cloak_autotune", load().cloak_autotune(ctx, n, ta, xa, ya, M, out_dtype, _stream(stream),
+                                                   C.byref(r)), ctx)
+    return {f: getattr(r, f) for f, _ in TuneResult._fields_}
+
+
+def cloak_tune_save(ctx, path: str):
+    _check("cloak_tune_save", load().cloak_tune_save(ctx, str(path).encode()), ctx)
+
+
+def cloak_tune_load(ctx, path: str) -> int:
+    n = C.c_int32(0)
+    _check("cloak_tune_load", load().cloak_tune_load(ctx, str(path).encode(), C.byref(n)), ctx)
+    return n.value
+
+
+def cloak_tune_clear(ctx):
+    _check("cloak_tune_clear", load().cloak_tune_clear(ctx), ctx)
 
 
 def cloak_rekey_begin(ctx, key: int, new_epoch: int, side_stream):
@@ -381,6 +416,26 @@ class CloakModel:
 
     def rekey(self, key, new_epoch, stream=None):
         cloak_rekey(self.ctx, key, new_epoch, stream)
+
+    def autotune(self, tensors, xs, ys=None, out_dtype=OUT_BF16, stream=None) -> dict:
+        """Tune the launch shape of linear_batch(tensors, xs) (ys overwritten)."""
+        import torch
+        M = xs[0].shape[0]
+        if ys is None:
+            ys = [torch.empty((M, self.model.tensors[t].n), device=xs[0].device,
+                              dtype=torch.float32 if out_dtype == OUT_F32 else torch.bfloat16)
+                  for t in tensors]
+        return cloak_autotune(self.ctx, list(tensors), [x.data_ptr() for x in xs],
+                              [y.data_ptr() for y in ys], M, out_dtype, stream)
+
+    def tune_save(self, path):
+        cloak_tune_save(self.ctx, path)
+
+    def tune_load(self, path) -> int:
+        return cloak_tune_load(self.ctx, path)
+
+    def tune_clear(self):
+        cloak_tune_clear(self.ctx)
 
     def rekey_begin(self, key, new_epoch, side_stream):
         cloak_rekey_begin(self.ctx, key, new_epoch, side_stream)

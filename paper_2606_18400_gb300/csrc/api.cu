@@ -431,6 +431,38 @@ extern "C" cloak_status cloak_rekey_advance(cloak_ctx *ctx, void *serve_stream, 
     return rekey_advance(ctx, (cudaStream_t)serve_stream, (cudaStream_t)side_stream, done);
 }
 
+extern "C" cloak_status cloak_autotune(cloak_ctx *ctx, int32_t n, const int32_t *tensors,
+                                      const void *const *x_dev, void *const *y_dev, int32_t M,
+                                      int32_t out_dtype, void *stream, cloak_tune_result *out) {
+    if (!ctx || n < 1 || n > 8 || !tensors || !x_dev || !y_dev || M < 1 || M > 65536 ||
+        (out_dtype != CLOAK_OUT_F32 && out_dtype != CLOAK_OUT_BF16))
+        return CLOAK_E_INVAL;
+    for (int i = 0; i < n; ++i) {
+        if (tensors[i] < 0 || tensors[i] >= (int32_t)ctx->tensors.size() || !x_dev[i] || !y_dev[i] ||
+            ((uintptr_t)x_dev[i] & 15))
+            return CLOAK_E_INVAL;
+    }
+    if (!ctx->keyed) return CLOAK_E_STATE;
+    CLOAK_CUDA(ctx, cudaSetDevice(ctx->device));
+    return autotune_run(ctx, n, tensors, x_dev, y_dev, M, out_dtype, (cudaStream_t)stream, out);
+}
+
+extern "C" cloak_status cloak_tune_save(const cloak_ctx *ctx, const char *path) {
+    if (!ctx || !path) return CLOAK_E_INVAL;
+    return tune_save(ctx, path);
+}
+
+extern "C" cloak_status cloak_tune_load(cloak_ctx *ctx, const char *path, int32_t *entries) {
+    if (!ctx || !path) return CLOAK_E_INVAL;
+    return tune_load(ctx, path, entries);
+}
+
+extern "C" cloak_status cloak_tune_clear(cloak_ctx *ctx) {
+    if (!ctx) return CLOAK_E_INVAL;
+    ctx->tune.clear();
+    return CLOAK_OK;
+}
+
 extern "C" cloak_status cloak_device_status(cloak_ctx *ctx) {
     if (!ctx) return CLOAK_E_INVAL;
     int st = 0;

@@ -6,6 +6,7 @@
 
 #include <cstdint>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/cloak.h"
@@ -24,6 +25,13 @@ struct TensorInfo {
     int64_t scale_off;           // offset of the tensor's FP8 scales
     int32_t row_off;             // offset of the tensor's tile rows (counters)
     int32_t layer;
+};
+
+// launch shape of the tensor-core linear: activation chunk (UMMA N), ring
+// depth, CTA count (0 = default for each)
+struct TuneCfg {
+    int32_t chunk = 0, stages = 0, grid = 0;
+    float us = 0.0f;                 // measured time of the launch sequence
 };
 
 // one independent Fisher-Yates problem of a batch
@@ -101,6 +109,11 @@ struct cloak_ctx {
     void *d_serve_ws = nullptr;                // serving-step workspace
     size_t serve_ws_cap = 0;
 
+    // autotuner: launch shapes per (dtype, shapes, M bucket, output type)
+    std::unordered_map<std::string, cloak::TuneCfg> tune;
+    const cloak::TuneCfg *tune_force = nullptr;  // set while the tuner measures
+    bool tune_invariant = false;                 // keep the default CTA split (serving)
+
     bool keyed = false, placed_any = false;
     uint64_t key = 0;
     uint32_t epoch = 0;
@@ -153,6 +166,16 @@ cloak_status serve_step_run(cloak_ctx *ctx, const cloak_serve_desc *d, const clo
                             cudaStream_t s);
 cloak_status stack_decode_run(cloak_ctx *ctx, const cloak_stack_desc *d, float *h, int M, int flags,
                               cudaStream_t s);
+// tune.cu
+cloak::TuneCfg tune_lookup(const cloak_ctx *ctx, int n, const int32_t *tensors, int M, int out_dtype);
+std::string tune_key(const cloak_ctx *ctx, int n, const int32_t *tensors, int M, int out_dtype);
+int tc_max_stages(bool fp8, int npad);
+int tc_stage_bytes(bool fp8, int npad);
+int tc_npad(int m);
+cloak_status autotune_run(cloak_ctx *ctx, int n, const int32_t *tensors, const void *const *xs,
+                          void *const *ys, int M, int out_dtype, cudaStream_t s, cloak_tune_result *res);
+cloak_status tune_save(const cloak_ctx *ctx, const char *path);
+cloak_status tune_load(cloak_ctx *ctx, const char *path, int32_t *entries);
 cloak_status linear_run_given_scratch(cloak_ctx *ctx, int t, const void *x, void *y, int M,
                                       int out_dtype, int flags, float *part, size_t part_floats,
                                       uint32_t *rowcnt, uint32_t max_grid, cudaStream_t s);

@@ -155,6 +155,7 @@ struct TcBatch {
     const uint32_t *slot_of;  // gather table; nullptr: uncloaked (slot = tile index)
     int np, M, out_f32, relu;
     int dep_wait;             // launched as a programmatic dependent of the quantiser
+    int stages;               // ring depth in use (1 .. TcCfg::STAGES)
     uint64_t total;           // units of all problems
     float *part;              // [grid][2][128][NPAD] partial sums
     int *status;
@@ -225,9 +226,10 @@ __global__ void __launch_bounds__(192, 1)
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + C::STAGES * C::STAGE);
-    uint64_t *empty = full + C::STAGES;
-    uint64_t *tfull = empty + C::STAGES;
+    const int NS = b.stages;
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + NS * C::STAGE);
+    uint64_t *empty = full + NS;
+    uint64_t *tfull = empty + NS;
     uint64_t *tempty = tfull + 2;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tempty + 2);
     volatile uint32_t *last_flag = tmem_slot + 1;
@@ -237,7 +239,7 @@ __global__ void __launch_bounds__(192, 1)
     const uint64_t u0 = blockIdx.x * T / G, u1 = (blockIdx.x + 1) * T / G;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < C::STAGES; ++s) {
+        for (int s = 0; s < NS; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
@@ -291,10 +293,10 @@ __global__ void __launch_bounds__(192, 1)
                 nxt = slot_for(b, u + 32 + lane, u1);
             }
             const uint32_t slot = __shfl_sync(0xffffffffu, cur, j);
-            const int s = it % C::STAGES;
-            const uint32_t ph = (it / C::STAGES) & 1;
+            const int s = it % NS;
+            const uint32_t ph = (it / NS) & 1;
             bool ok = true;
-            if (lane == 0 && it >= (uint32_t)C::STAGES) {
+            if (lane == 0 && it >= (uint32_t)NS) {
                 if (!waited) release();
                 ok = mbar_wait(&empty[s], ph ^ 1, b.status);
             }
@@ -338,8 +340,8 @@ __global__ void __launch_bounds__(192, 1)
                 tc_fence_after();
                 const uint32_t d = tmem + bf * NPAD;
                 for (uint64_t uu = u; uu < send; ++uu, ++it) {
-                    const int s = it % C::STAGES;
-                    if (!mbar_wait(&full[s], (it / C::STAGES) & 1, b.status)) { ok = false; break; }
+                    const int s = it % NS;
+                    if (!mbar_wait(&full[s], (it / NS) & 1, b.status)) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t sa = smem_u32(smem + s * C::STAGE), sb = sa + C::A_BYTES;
 #pragma unroll
@@ -466,7 +468,7 @@ __global__ void __launch_bounds__(192, 1)
 
 template <bool FP8, int NPAD>
 static cloak_status launch_tc(cloak_ctx *ctx, const CUtensorMap &tw, const void *const *xs,
-                              TcBatch &b, cudaStream_t s) {
+                              TcBatch &b, const TuneCfg &cfg, cudaStream_t s) {
     using C = TcCfg<FP8, NPAD>;
     static bool attr_set = false;  // per instantiation; once per process
     if (!attr_set) {
@@ -484,7 +486,10 @@ static cloak_status launch_tc(cloak_ctx *ctx, const CUtensorMap &tw, const void 
             return CLOAK_E_CUDA;
         }
     }
-    const uint32_t grid = (uint32_t)std::min<uint64_t>(b.total, (uint64_t)ctx->sm_count);
+    b.stages = (cfg.stages >= 1 && cfg.stages <= C::STAGES) ? cfg.stages : C::STAGES;
+    const uint32_t want = cfg.grid > 0 ? (uint32_t)cfg.grid : (uint32_t)ctx->sm_count;
+    const uint32_t grid = (uint32_t)std::min<uint64_t>(b.total, want);
+    const size_t smem = (size_t)b.stages * C::STAGE + 1024 + 512;
     const size_t need = (size_t)grid * 2 * 128 * NPAD;
     if (need > ctx->part_cap) {
         if (ctx->d_part) CLOAK_CUDA(ctx, cudaFree(ctx->d_part));
@@ -494,19 +499,19 @@ static cloak_status launch_tc(cloak_ctx *ctx, const CUtensorMap &tw, const void 
     }
     b.part = ctx->d_part;
     if (b.dep_wait) {
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(grid);
-        cfg.blockDim = dim3(192);
-        cfg.dynamicSmemBytes = C::SMEM;
-        cfg.stream = s;
+        cudaLaunchConfig_t lc = {};
+        lc.gridDim = dim3(grid);
+        lc.blockDim = dim3(192);
+        lc.dynamicSmemBytes = smem;
+        lc.stream = s;
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
         attr[0].val.programmaticStreamSerializationAllowed = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        CLOAK_CUDA(ctx, cudaLaunchKernelEx(&cfg, k_linear_tc<FP8, NPAD>, tw, tx, b));
+        lc.attrs = attr;
+        lc.numAttrs = 1;
+        CLOAK_CUDA(ctx, cudaLaunchKernelEx(&lc, k_linear_tc<FP8, NPAD>, tw, tx, b));
     } else {
-        k_linear_tc<FP8, NPAD><<<grid, 192, C::SMEM, s>>>(tw, tx, b);
+        k_linear_tc<FP8, NPAD><<<grid, 192, smem, s>>>(tw, tx, b);
     }
     CLOAK_LAUNCHED(ctx);
     return CLOAK_OK;
@@ -514,13 +519,27 @@ static cloak_status launch_tc(cloak_ctx *ctx, const CUtensorMap &tw, const void 
 
 template <bool FP8>
 static cloak_status dispatch_tc(cloak_ctx *ctx, const CUtensorMap &tw, const void *const *xs,
-                                TcBatch &b, cudaStream_t s) {
-    if (b.M <= 16) return launch_tc<FP8, 16>(ctx, tw, xs, b, s);
-    if (b.M <= 32) return launch_tc<FP8, 32>(ctx, tw, xs, b, s);
-    if (b.M <= 64) return launch_tc<FP8, 64>(ctx, tw, xs, b, s);
-    if (b.M <= 128) return launch_tc<FP8, 128>(ctx, tw, xs, b, s);
-    return launch_tc<FP8, 256>(ctx, tw, xs, b, s);
+                                TcBatch &b, const TuneCfg &cfg, cudaStream_t s) {
+    if (b.M <= 16) return launch_tc<FP8, 16>(ctx, tw, xs, b, cfg, s);
+    if (b.M <= 32) return launch_tc<FP8, 32>(ctx, tw, xs, b, cfg, s);
+    if (b.M <= 64) return launch_tc<FP8, 64>(ctx, tw, xs, b, cfg, s);
+    if (b.M <= 128) return launch_tc<FP8, 128>(ctx, tw, xs, b, cfg, s);
+    return launch_tc<FP8, 256>(ctx, tw, xs, b, cfg, s);
 }
+
+int tc_max_stages(bool fp8, int npad) {
+    switch (npad) {
+        case 16: return fp8 ? TcCfg<true, 16>::STAGES : TcCfg<false, 16>::STAGES;
+        case 32: return fp8 ? TcCfg<true, 32>::STAGES : TcCfg<false, 32>::STAGES;
+        case 64: return fp8 ? TcCfg<true, 64>::STAGES : TcCfg<false, 64>::STAGES;
+        case 128: return fp8 ? TcCfg<true, 128>::STAGES : TcCfg<false, 128>::STAGES;
+        default: return fp8 ? TcCfg<true, 256>::STAGES : TcCfg<false, 256>::STAGES;
+    }
+}
+
+int tc_stage_bytes(bool fp8, int npad) { return (fp8 ? 16384 : 32768) + npad * (fp8 ? 128 : 256); }
+
+int tc_npad(int m) { return m <= 16 ? 16 : m <= 32 ? 32 : m <= 64 ? 64 : m <= 128 ? 128 : 256; }
 
 cloak_status linear_batch_run(cloak_ctx *ctx, int n, const int32_t *tensors, const void *const *xs,
                               void *const *ys, int M, int out_dtype, int flags, cudaStream_t s) {
@@ -543,9 +562,13 @@ cloak_status linear_batch_run(cloak_ctx *ctx, int n, const int32_t *tensors, con
     }
     const bool fp8 = ctx->dtype == CLOAK_E4M3;
     const CUtensorMap &tw = unc ? ctx->tmap_twin : ctx->tmap_arena;
+    // launch shape: forced (tuner measuring), tuned, or the default
+    TuneCfg cfg = tune_lookup(ctx, n, tensors, M, out_dtype);
+    if (ctx->tune_invariant) cfg.grid = 0;  // the split over CTAs fixes the summation order
+    const int chunk = cfg.chunk > 0 ? cfg.chunk : 256;
     if (fp8) {
         size_t qb = 0;
-        for (int p = 0; p < n; ++p) qb += (size_t)std::min(M, 256) * ctx->info[tensors[p]].k;
+        for (int p = 0; p < n; ++p) qb += (size_t)std::min(M, chunk) * ctx->info[tensors[p]].k;
         if (qb > ctx->xq_cap) {
             if (ctx->d_xq) CLOAK_CUDA(ctx, cudaFree(ctx->d_xq));
             ctx->d_xq = nullptr;
@@ -554,8 +577,8 @@ cloak_status linear_batch_run(cloak_ctx *ctx, int n, const int32_t *tensors, con
         }
         if (!ctx->d_xs) CLOAK_CUDA(ctx, cudaMalloc(&ctx->d_xs, MAXP * 256 * sizeof(float)));
     }
-    for (int m0 = 0; m0 < M; m0 += 256) {
-        const int mb = std::min(256, M - m0);
+    for (int m0 = 0; m0 < M; m0 += chunk) {
+        const int mb = std::min(chunk, M - m0);
         TcBatch b{};
         b.slot_of = slot_of;
         b.np = n;
@@ -602,7 +625,8 @@ cloak_status linear_batch_run(cloak_ctx *ctx, int n, const int32_t *tensors, con
             CLOAK_LAUNCHED(ctx);
             b.dep_wait = 1;
         }
-        cloak_status rc = fp8 ? dispatch_tc<true>(ctx, tw, xm, b, s) : dispatch_tc<false>(ctx, tw, xm, b, s);
+        cloak_status rc = fp8 ? dispatch_tc<true>(ctx, tw, xm, b, cfg, s)
+                              : dispatch_tc<false>(ctx, tw, xm, b, cfg, s);
         if (rc) return rc;
     }
     return CLOAK_OK;
@@ -627,6 +651,7 @@ static cloak_status launch_tc_given(cloak_ctx *ctx, const CUtensorMap &tw, const
     const uint32_t grid = (uint32_t)std::min<uint64_t>(
         b.total, std::min<uint64_t>((uint64_t)ctx->sm_count, (uint64_t)max_grid));
     if ((size_t)grid * 2 * 128 * NPAD > part_floats) return CLOAK_E_INVAL;
+    b.stages = C::STAGES;
     k_linear_tc<false, NPAD><<<grid, 192, C::SMEM, s>>>(tw, tx, b);
     CLOAK_LAUNCHED(ctx);
     return CLOAK_OK;

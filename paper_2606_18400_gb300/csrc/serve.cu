@@ -361,8 +361,22 @@ __global__ void k_argmax(const float *logits, int V, int32_t *out) {
     }
 }
 
+static cloak_status serve_step_body(cloak_ctx *ctx, const cloak_serve_desc *d,
+                                    const cloak_serve_batch *b, cudaStream_t s);
+
+// The linears keep the default CTA split here (tuned chunk and ring depth do
+// not change a sum's order): a token computes the same in any batch.
 cloak_status serve_step_run(cloak_ctx *ctx, const cloak_serve_desc *d, const cloak_serve_batch *b,
                             cudaStream_t s) {
+    const bool was = ctx->tune_invariant;
+    ctx->tune_invariant = true;
+    const cloak_status rc = serve_step_body(ctx, d, b, s);
+    ctx->tune_invariant = was;
+    return rc;
+}
+
+static cloak_status serve_step_body(cloak_ctx *ctx, const cloak_serve_desc *d,
+                                    const cloak_serve_batch *b, cudaStream_t s) {
     const cloak_stack_desc &sd = d->stack;
     if (ctx->dtype != CLOAK_BF16 || sd.head_dim != 128) return CLOAK_E_UNSUPPORTED;
     const int M = b->num_tokens, S = b->num_sample;
