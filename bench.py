@@ -323,6 +323,10 @@ def bench_extras(cloak, synth, torch, dev, stream, key, steps, tune=True):
     for M in (1, 8, 32, 64):
         h0 = torch.from_numpy(synth.activations_host(M, 4096, seed=M)).cuda()
         res = {}
+        if tune:
+            r = cm.autotune_stack(h0, desc=desc, stream=stream.cuda_stream)
+            res["l2_prefetch"] = {"tiles_per_cta": r["l2_prefetch"], "tuned_ms": round(r["us"] / 1e3, 4),
+                                  "default_ms": round(r["default_us"] / 1e3, 4)}
         for name, unc in (("cloaked", False), ("uncloaked", True)):
             hb = h0.clone()
             def fn(hb=hb, unc=unc):
@@ -339,7 +343,8 @@ def bench_extras(cloak, synth, torch, dev, stream, key, steps, tune=True):
         stk[str(M)] = {"cloaked_ms": round(res["cloaked"], 4), "uncloaked_ms": round(res["uncloaked"], 4),
                        "cloaked_gbs": round(bytes_step / (res["cloaked"] / 1e3) / 1e9, 1),
                        "uncloaked_gbs": round(bytes_step / (res["uncloaked"] / 1e3) / 1e9, 1),
-                       "tokens_per_s": round(M / (res["cloaked"] / 1e3), 1)}
+                       "tokens_per_s": round(M / (res["cloaked"] / 1e3), 1),
+                       "l2_prefetch": res.get("l2_prefetch")}
     assert cm.device_status() == 0
     out["stack_decode_llama7b_32L"] = stk
     ts = []
@@ -641,7 +646,11 @@ def run_profile(args):
     """Small cases of one kernel each, for ncu captures (a few GB at most):
     stack  -- a 4-layer 7B-class stack (1.6 GB), decode M=1, 3 launches;
     fp8    -- one GQA E4M3 layer (233 MB), grouped decode M=1, 3 launches;
-    prefill-- one 7B-class layer, grouped M=512, 3 launches."""
+    prefill-- one 7B-class layer, grouped M=512, 3 launches;
+    decode -- one 7B-class layer, grouped M=1 (the headline step), 3 launches.
+    The linears' launch shape is tuned first (unless --no-tune); the profiled
+    launches sit inside the NVTX range "profiled" (ncu --nvtx
+    --nvtx-include "profiled/")."""
     import torch
     from paper_2606_18400_gb300 import cloak, synth
     cloak.load()
@@ -659,14 +668,24 @@ def run_profile(args):
     torch.cuda.synchronize()
     if args.profile == "stack":
         h0 = torch.from_numpy(synth.activations_host(1, 4096, seed=1)).cuda()
+        torch.cuda.nvtx.range_push("profiled")
         for _ in range(3):
             cm.stack_decode(h0.clone())
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
     else:
-        M = 1 if args.profile == "fp8" else 512
+        M = 512 if args.profile == "prefill" else 1
         xs = [torch.from_numpy(synth.activations_host(M, t.k, seed=i)).cuda().to(torch.bfloat16)
               for i, t in enumerate(model.tensors)]
+        group = list(range(len(model.tensors)))
+        shape = None if args.no_tune else cm.autotune(group, xs)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("profiled")
         for _ in range(3):
-            cm.linear_batch(list(range(len(model.tensors))), xs)
+            cm.linear_batch(group, xs)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        print(json.dumps({"launch_shape": shape}))
     torch.cuda.synchronize()
     assert cm.device_status() == 0
     cm.close()
@@ -684,7 +703,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--serve", action="store_true", help="run the serving sweep instead")
-    ap.add_argument("--profile", choices=["stack", "fp8", "prefill"], help="small case for ncu")
+    ap.add_argument("--profile", choices=["stack", "fp8", "prefill", "decode"],
+                    help="small case for ncu")
     ap.add_argument("--rates", default="2,8,32")
     ap.add_argument("--serve-seconds", type=float, default=30.0)
     ap.add_argument("--drain-seconds", type=float, default=30.0)

@@ -300,12 +300,21 @@ typedef struct {
     float us;             /* time of the chosen shape, microseconds             */
     float default_us;     /* time of the default shape                          */
     int32_t candidates;   /* shapes measured                                    */
+    int32_t l2_prefetch;  /* layer stack: next-stage tiles per CTA pulled into
+                             L2 during a stage's tail (-1 for linears)         */
 } cloak_tune_result;
 CLOAK_API cloak_status cloak_autotune(cloak_ctx *ctx, int32_t n, const int32_t *tensors,
                                       const void *const *x_dev, void *const *y_dev, int32_t M,
                                       int32_t out_dtype, void *stream, cloak_tune_result *out);
-/* Write the tuned shapes as JSON lines ({"chunk", "stages", "grid", "us",
- * "key"}) / read such a file, adding its entries (count in *entries). A key
+/* Tune the layer-stack launch (cloak_stack_decode) for `desc` and M: times
+ * its L2 prefetch depths (0 to 48 tiles per CTA) on a copy of h_dev (h_dev is
+ * not changed) and keeps the fastest for (layers, d_model, d_ff, M bucket).
+ * Key: "stack L<layers> d<d_model> f<d_ff> m<bucket>". */
+CLOAK_API cloak_status cloak_autotune_stack(cloak_ctx *ctx, const cloak_stack_desc *desc,
+                                            const float *h_dev, int32_t M, void *stream,
+                                            cloak_tune_result *out);
+/* Write the tuned shapes as JSON lines ({"chunk", "stages", "grid", "l2pf",
+ * "us", "key"}) / read such a file, adding its entries (count in *entries). A key
  * reads "<bf16|e4m3> m<bucket> <N>x<K> ..." (the bucket is the UMMA N for
  * M <= 256: 16, 32, 64, 128 or 256; above, M rounded up to 256; then each
  * weight's shape in call order).

@@ -63,7 +63,7 @@ class ServeDesc(C.Structure):
 
 class TuneResult(C.Structure):
     _fields_ = [("chunk", C.c_int32), ("stages", C.c_int32), ("grid", C.c_int32), ("us", C.c_float),
-                ("default_us", C.c_float), ("candidates", C.c_int32)]
+                ("default_us", C.c_float), ("candidates", C.c_int32), ("l2_prefetch", C.c_int32)]
 
 
 class ServeBatch(C.Structure):
@@ -98,6 +98,7 @@ SIGNATURES = [
     ("cloak_rekey_begin", _i32, [_vp, _u64, _u32, _vp]),
     ("cloak_autotune", _i32, [_vp, _i32, C.POINTER(_i32), C.POINTER(_vp), C.POINTER(_vp), _i32, _i32, _vp,
                               C.POINTER(TuneResult)]),
+    ("cloak_autotune_stack", _i32, [_vp, C.POINTER(StackDesc), _vp, _i32, _vp, C.POINTER(TuneResult)]),
     ("cloak_tune_save", _i32, [_vp, C.c_char_p]),
     ("cloak_tune_load", _i32, [_vp, C.c_char_p, C.POINTER(_i32)]),
     ("cloak_tune_clear", _i32, [_vp]),
@@ -244,6 +245,13 @@ def cloak_autotune(ctx, tensors, x_devs, y_devs, M: int, out_dtype: int, stream=
     r = TuneResult()
     _check("cloak_autotune", load().cloak_autotune(ctx, n, ta, xa, ya, M, out_dtype, _stream(stream),
                                                    C.byref(r)), ctx)
+    return {f: getattr(r, f) for f, _ in TuneResult._fields_}
+
+
+def cloak_autotune_stack(ctx, desc, h_dev: int, M: int, stream=None) -> dict:
+    r = TuneResult()
+    _check("cloak_autotune_stack", load().cloak_autotune_stack(ctx, C.byref(desc), h_dev, M, _stream(stream),
+                                                               C.byref(r)), ctx)
     return {f: getattr(r, f) for f, _ in TuneResult._fields_}
 
 
@@ -416,6 +424,10 @@ class CloakModel:
 
     def rekey(self, key, new_epoch, stream=None):
         cloak_rekey(self.ctx, key, new_epoch, stream)
+
+    def autotune_stack(self, h, desc=None, stream=None) -> dict:
+        """Tune the layer-stack launch for h's batch (h is not changed)."""
+        return cloak_autotune_stack(self.ctx, desc or self.stack_desc(), h.data_ptr(), h.shape[0], stream)
 
     def autotune(self, tensors, xs, ys=None, out_dtype=OUT_BF16, stream=None) -> dict:
         """Tune the launch shape of linear_batch(tensors, xs) (ys overwritten)."""

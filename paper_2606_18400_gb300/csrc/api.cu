@@ -447,6 +447,15 @@ extern "C" cloak_status cloak_autotune(cloak_ctx *ctx, int32_t n, const int32_t 
     return autotune_run(ctx, n, tensors, x_dev, y_dev, M, out_dtype, (cudaStream_t)stream, out);
 }
 
+extern "C" cloak_status cloak_autotune_stack(cloak_ctx *ctx, const cloak_stack_desc *desc,
+                                            const float *h_dev, int32_t M, void *stream,
+                                            cloak_tune_result *out) {
+    if (!ctx || !desc || !desc->layer_tensors || !h_dev || ((uintptr_t)h_dev & 15)) return CLOAK_E_INVAL;
+    if (!ctx->keyed || ctx->rk.active) return CLOAK_E_STATE;
+    CLOAK_CUDA(ctx, cudaSetDevice(ctx->device));
+    return autotune_stack_run(ctx, desc, h_dev, M, (cudaStream_t)stream, out);
+}
+
 extern "C" cloak_status cloak_tune_save(const cloak_ctx *ctx, const char *path) {
     if (!ctx || !path) return CLOAK_E_INVAL;
     return tune_save(ctx, path);

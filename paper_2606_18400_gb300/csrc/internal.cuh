@@ -31,6 +31,7 @@ struct TensorInfo {
 // depth, CTA count (0 = default for each)
 struct TuneCfg {
     int32_t chunk = 0, stages = 0, grid = 0;
+    int32_t l2pf = -1;               // layer-stack kernel: L2 prefetch depth (-1: default)
     float us = 0.0f;                 // measured time of the launch sequence
 };
 
@@ -106,6 +107,7 @@ struct cloak_ctx {
     void *d_stack_ws = nullptr;                // layer-stack decode workspace
     size_t stack_ws_cap = 0;
     std::vector<uint8_t> stack_sig;            // stage program last uploaded
+    int stack_l2_pf_force = -1;                // set while the tuner measures the stack kernel
     void *d_serve_ws = nullptr;                // serving-step workspace
     size_t serve_ws_cap = 0;
 
@@ -174,6 +176,9 @@ int tc_stage_bytes(bool fp8, int npad);
 int tc_npad(int m);
 cloak_status autotune_run(cloak_ctx *ctx, int n, const int32_t *tensors, const void *const *xs,
                           void *const *ys, int M, int out_dtype, cudaStream_t s, cloak_tune_result *res);
+cloak_status autotune_stack_run(cloak_ctx *ctx, const cloak_stack_desc *d, const float *h, int M,
+                                cudaStream_t s, cloak_tune_result *res);
+int stack_l2_prefetch(const cloak_ctx *ctx, const cloak_stack_desc *d, int M);
 cloak_status tune_save(const cloak_ctx *ctx, const char *path);
 cloak_status tune_load(cloak_ctx *ctx, const char *path, int32_t *entries);
 cloak_status linear_run_given_scratch(cloak_ctx *ctx, int t, const void *x, void *y, int M,

@@ -234,4 +234,9 @@ __host__ __device__ constexpr uint32_t idesc_make(uint32_t ab_fmt, uint32_t M, u
            | ((M >> 4) << 24);       // M / 16
 }
 
+// L2 prefetch of a global range (16-byte aligned address and size)
+__device__ __forceinline__ void prefetch_l2_bulk(const void *p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 }  // namespace cloak

@@ -55,6 +55,8 @@ struct StackArgs {
     int nstages, M, D;
     float eps;
     const uint32_t *slot_of;  // nullptr: uncloaked twin
+    const uint8_t *wbase;     // arena (or twin): tile at wbase + slot * 32 KiB
+    int l2_pf;                // next-stage tiles per CTA prefetched into L2 (0: none)
     float *h;                 // FP32 residual [M, D]
     __nv_bfloat16 *hb;        // its BF16 copy (the activation operand)
     float *part;              // [grid][2][2][128][NPAD]
@@ -317,6 +319,21 @@ __global__ void __launch_bounds__(192, 1)
                 if (ok) flush();
             }
             ok = __shfl_sync(0xffffffffu, (int)ok, 0) != 0;
+            // Every tile of this stage is requested; what remains of it is the
+            // ring in flight, the MMAs, the epilogue and the barrier, while HBM
+            // would idle. Pull the next stage's tiles beyond the ring (those the
+            // ring takes first are requested as its slots free) into L2.
+            if (ok && si + 1 < a.nstages && a.l2_pf > 0) {
+                const StackStage &nx = a.stages[si + 1];
+                const uint64_t n0 = blockIdx.x * nx.total / G, n1 = (blockIdx.x + 1) * nx.total / G;
+                for (int k = lane; k < a.l2_pf; k += 32) {
+                    const uint64_t u = n0 + C::STAGES + (uint64_t)k;
+                    if (u < n1) {
+                        const uint32_t slot = stack_slot(a, nx, u, n1);
+                        prefetch_l2_bulk(a.wbase + (size_t)slot * 32768u, 32768u);
+                    }
+                }
+            }
         }
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA
@@ -735,6 +752,8 @@ cloak_status stack_decode_run(cloak_ctx *ctx, const cloak_stack_desc *d, float *
     a.D = D;
     a.eps = d->rms_eps;
     a.slot_of = unc ? nullptr : ctx->d_tile_slot;
+    a.wbase = unc ? ctx->twin : ctx->arena;
+    a.l2_pf = stack_l2_prefetch(ctx, d, M);
     a.h = h;
     a.hb = hb;
     a.part = part;

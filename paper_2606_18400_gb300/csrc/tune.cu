@@ -12,6 +12,10 @@
 // them keep the same summation order; the serving step uses the tuned chunk and ring depth but
 // the default CTA count, so that a token's result does not depend on its
 // batch. Entries persist as JSON lines.
+//
+// The layer-stack kernel has one more depth to choose: how many of the next
+// stage's weight tiles each CTA pulls into L2 while the current stage drains
+// and the grid barrier is pending (beyond the tiles its smem ring takes).
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -143,6 +147,87 @@ cloak_status autotune_run(cloak_ctx *ctx, int n, const int32_t *tensors, const v
         res->us = best.us;
         res->default_us = t_default;
         res->candidates = (int32_t)cand.size();
+        res->l2_prefetch = -1;
+    }
+    return CLOAK_OK;
+}
+
+static std::string stack_key(const cloak_stack_desc *d, int M) {
+    return "stack L" + std::to_string(d->num_layers) + " d" + std::to_string(d->d_model) + " f" +
+           std::to_string(d->d_ff) + " m" + std::to_string(m_bucket(M));
+}
+
+constexpr int STACK_L2PF_DEFAULT = 16;
+
+int stack_l2_prefetch(const cloak_ctx *ctx, const cloak_stack_desc *d, int M) {
+    if (ctx->stack_l2_pf_force >= 0) return ctx->stack_l2_pf_force;
+    if (!ctx->tune.empty()) {
+        auto it = ctx->tune.find(stack_key(d, M));
+        if (it != ctx->tune.end() && it->second.l2pf >= 0) return it->second.l2pf;
+    }
+    return STACK_L2PF_DEFAULT;
+}
+
+cloak_status autotune_stack_run(cloak_ctx *ctx, const cloak_stack_desc *d, const float *h, int M,
+                                cudaStream_t s, cloak_tune_result *res) {
+    if (M < 1 || M > 64 || d->d_model <= 0) return CLOAK_E_INVAL;
+    const size_t hb = (size_t)M * d->d_model * sizeof(float);
+    float *hs = nullptr;
+    CLOAK_CUDA(ctx, cudaMalloc(&hs, hb));  // the kernel updates h in place: run on a copy
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cloak_status rc = CLOAK_OK;
+    const int cand[] = {0, 8, 16, 24, 32, 48};
+    const int nc = (int)(sizeof cand / sizeof cand[0]);
+    float us[sizeof cand / sizeof cand[0]] = {};
+    auto run = [&](int reps) -> cloak_status {
+        for (int r = 0; r < reps; ++r) {
+            if (cudaMemcpyAsync(hs, h, hb, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+                return cuda_fail(ctx, cudaGetLastError(), "stack tuner copy");
+            cloak_status q = stack_decode_run(ctx, d, hs, M, 0, s);
+            if (q) return q;
+        }
+        return CLOAK_OK;
+    };
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = CLOAK_E_CUDA;
+    for (int pass = 0; pass < 2 && !rc; ++pass) {  // two passes, keep each candidate's best
+        for (int i = 0; i < nc && !rc; ++i) {
+            ctx->stack_l2_pf_force = cand[i];
+            rc = run(1);
+            if (!rc) {
+                cudaEventRecord(e0, s);
+                rc = run(5);
+                cudaEventRecord(e1, s);
+            }
+            if (!rc && cudaEventSynchronize(e1) == cudaSuccess) {
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                const float t = 1e3f * ms / 5.0f;
+                us[i] = pass == 0 ? t : std::min(us[i], t);
+            }
+        }
+    }
+    ctx->stack_l2_pf_force = -1;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(hs);
+    if (rc) return rc;
+    int best = 0, dflt = 0;
+    for (int i = 0; i < nc; ++i) {
+        if (us[i] < us[best]) best = i;
+        if (cand[i] == STACK_L2PF_DEFAULT) dflt = i;
+    }
+    TuneCfg c;
+    c.l2pf = cand[best];
+    c.us = us[best];
+    ctx->tune[stack_key(d, M)] = c;
+    if (res) {
+        res->chunk = 0;
+        res->stages = 0;
+        res->grid = ctx->sm_count;
+        res->us = us[best];
+        res->default_us = us[dflt];
+        res->candidates = nc;
+        res->l2_prefetch = cand[best];
     }
     return CLOAK_OK;
 }
@@ -155,8 +240,10 @@ cloak_status tune_save(const cloak_ctx *ctx, const char *path) {
     std::sort(keys.begin(), keys.end());
     for (const auto &k : keys) {
         const TuneCfg &c = ctx->tune.at(k);
-        std::fprintf(f, "{\"chunk\": %d, \"stages\": %d, \"grid\": %d, \"us\": %.3f, \"key\": \"%s\"}\n",
-                     c.chunk, c.stages, c.grid, c.us, k.c_str());
+        std::fprintf(f,
+                     "{\"chunk\": %d, \"stages\": %d, \"grid\": %d, \"l2pf\": %d, \"us\": %.3f, "
+                     "\"key\": \"%s\"}\n",
+                     c.chunk, c.stages, c.grid, c.l2pf, c.us, k.c_str());
     }
     return std::fclose(f) == 0 ? CLOAK_OK : CLOAK_E_INVAL;
 }
@@ -171,10 +258,12 @@ cloak_status tune_load(cloak_ctx *ctx, const char *path, int32_t *entries) {
         if (line[0] != '{') continue;
         TuneCfg c;
         char key[900];
-        if (std::sscanf(line, "{\"chunk\": %d, \"stages\": %d, \"grid\": %d, \"us\": %f, \"key\": \"%899[^\"]\"}",
-                        &c.chunk, &c.stages, &c.grid, &c.us, key) != 5 ||
+        if (std::sscanf(line,
+                        "{\"chunk\": %d, \"stages\": %d, \"grid\": %d, \"l2pf\": %d, \"us\": %f, "
+                        "\"key\": \"%899[^\"]\"}",
+                        &c.chunk, &c.stages, &c.grid, &c.l2pf, &c.us, key) != 6 ||
             c.chunk < 0 || c.chunk > 65536 || c.stages < 0 || c.stages > 16 || c.grid < 0 ||
-            c.grid > 65535) {
+            c.grid > 65535 || c.l2pf < -1 || c.l2pf > 1024) {
             rc = CLOAK_E_INVAL;
             break;
         }

@@ -45,7 +45,7 @@ def test_hand_written_shapes_keep_parity(cloak_lib, tmp_path, dtype, shape):
     with open(f, "w") as fh:
         for M in Ms:
             for t in range(len(m.tensors)):
-                fh.write(json.dumps({**SHAPES[shape], "us": 0.0, "key": key(m, t, M)}) + "\n")
+                fh.write(json.dumps({**SHAPES[shape], "l2pf": -1, "us": 0.0, "key": key(m, t, M)}) + "\n")
     assert cm.tune_load(f) == len(Ms) * len(m.tensors)
     for M in Ms:
         for t in range(len(m.tensors)):
@@ -77,7 +77,7 @@ def test_autotune_chooses_measures_and_persists(cloak_lib, tmp_path):
     f = tmp_path / "tuned.jsonl"
     cm.tune_save(f)
     lines = [json.loads(l) for l in open(f)]
-    assert len(lines) == 2 and all(set(l) == {"chunk", "stages", "grid", "us", "key"} for l in lines)
+    assert len(lines) == 2 and all(set(l) == {"chunk", "stages", "grid", "l2pf", "us", "key"} for l in lines)
     cm.tune_clear()
     assert cm.tune_load(f) == 2
     for M, (xs, ref) in outs.items():                  # the same shapes again: the same bits
@@ -86,9 +86,45 @@ def test_autotune_chooses_measures_and_persists(cloak_lib, tmp_path):
         for a, b in zip(ys, ref):
             assert torch.equal(a.cpu(), b)
     bad = tmp_path / "bad.jsonl"
-    bad.write_text('{"chunk": 64, "stages": 99, "grid": 1, "us": 0, "key": "bf16 m16 512x512"}\n')
+    bad.write_text('{"chunk": 64, "stages": 99, "grid": 1, "l2pf": -1, "us": 0, "key": "bf16 m16 512x512"}\n')
     with pytest.raises(cloak_lib.CloakError):
         cm.tune_load(bad)
     with pytest.raises(cloak_lib.CloakError):
         cm.tune_load(tmp_path / "missing.jsonl")
+    cm.close()
+
+
+@pytest.mark.parametrize("l2pf", [None, 0, 48])
+def test_stack_l2_prefetch_depths_keep_parity(cloak_lib, tmp_path, l2pf):
+    """The stack kernel's L2 prefetch depth (tuned, none, or more tiles than a
+    CTA has) changes no bit of the result; the tuner leaves h untouched."""
+    import oracle as O
+    m = synth.small_decoder(3, synth.DT_BF16, d_model=512, n_heads=4, n_kv_heads=2, d_ff=320,
+                            head_dim=128, spare_pages=3)
+    cm, om, tb, arena, scales, Ws = place_both(cloak_lib, m, key=0x5EED)
+    M = 5
+    h0 = synth.activations_host(M, m.d_model, seed=2)
+    ref_dev = torch.from_numpy(h0).cuda()
+    cm.stack_decode(ref_dev)                        # default depth
+    torch.cuda.synchronize()
+    if l2pf is None:
+        h = torch.from_numpy(h0).cuda()
+        r = cm.autotune_stack(h)
+        torch.cuda.synchronize()
+        assert torch.equal(h.cpu(), torch.from_numpy(h0))
+        assert r["l2_prefetch"] in (0, 8, 16, 24, 32, 48) and r["us"] > 0
+    else:
+        f = tmp_path / "stack.jsonl"
+        f.write_text(json.dumps({"chunk": 0, "stages": 0, "grid": 0, "l2pf": l2pf, "us": 0.0,
+                                 "key": f"stack L3 d512 f320 m{bucket(M)}"}) + "\n")
+        assert cm.tune_load(f) == 1
+    h = torch.from_numpy(h0).cuda()
+    cm.stack_decode(h)
+    hu = torch.from_numpy(h0).cuda()
+    cm.stack_decode(hu, uncloaked=True)
+    torch.cuda.synchronize()
+    assert cm.device_status() == 0
+    assert torch.equal(h, ref_dev) and torch.equal(h, hu)
+    W64 = [O.bf16_value(O.bf16_bits(w)) for w in Ws]
+    assert O.relative_error(h.cpu().numpy(), O.stack_decode_f64(m, W64, h0)) <= 1e-2
     cm.close()
