@@ -139,7 +139,7 @@ __device__ __forceinline__ bool grid_wait(const StackArgs &a, uint32_t target) {
     if (ld_acquire(a.bar) >= target) return true;
     const unsigned long long t0 = globaltimer();
     while (ld_acquire(a.bar) < target) {
-        __nanosleep(32);
+        __nanosleep(64);  // one poller per CTA; keep the counter's L2 line quiet
         if (aborted(a.abort)) return false;
         if (globaltimer() - t0 > WAIT_LIMIT_NS) {
             give_up(a);
@@ -166,6 +166,19 @@ __device__ __forceinline__ bool bar_wait(const StackArgs &a, uint64_t *bar, uint
 
 __device__ __forceinline__ void fence_proxy_async_global() {
     asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+// The epilogue's first thread is the CTA's only poller of the grid barrier; it
+// publishes the stage whose inputs are complete to the producer in shared
+// memory (STAGE_ABORT: the launch gave up).
+constexpr uint32_t STAGE_ABORT = 0xFFFFFFFFu;
+__device__ __forceinline__ uint32_t ld_acquire_cta(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"(smem_u32(p)) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_cta(uint32_t *p, uint32_t v) {
+    asm volatile("st.release.cta.shared::cta.u32 [%0], %1;" ::"r"(smem_u32(p)), "r"(v) : "memory");
 }
 
 __device__ __forceinline__ float silu(float g) { return g / (1.0f + expf(-g)); }
@@ -202,6 +215,7 @@ __global__ void __launch_bounds__(192, 1)
     uint64_t *tempty = tfull + 2;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tempty + 2);
     volatile uint32_t *last_flag = tmem_slot + 1;
+    uint32_t *stage_open = tmem_slot + 2;  // highest stage whose inputs are complete
     float *rstd = reinterpret_cast<float *>(tmem_slot + 4);  // [NPAD]
     float *ss_w = rstd + 64;                                   // [4][16] per-warp chunk sums
 
@@ -209,6 +223,7 @@ __global__ void __launch_bounds__(192, 1)
     const uint64_t G = gridDim.x;
 
     if (threadIdx.x == 0) {
+        *stage_open = 0;
         for (int s = 0; s < C::STAGES; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
@@ -256,8 +271,16 @@ __global__ void __launch_bounds__(192, 1)
             const StackStage &st = a.stages[si];
             const uint64_t T = st.total;
             const uint64_t u0 = blockIdx.x * T / G, u1 = (blockIdx.x + 1) * T / G;
-            const uint32_t target = (uint32_t)(si * G);
-            bool passed = (si == 0) || ld_acquire(a.bar) >= target;
+            const uint32_t sidx = (uint32_t)si;
+            // stage si's inputs are complete once the epilogue has seen the grid
+            // barrier pass and published it
+            auto is_open = [&]() -> bool {
+                const uint32_t v = ld_acquire_cta(stage_open);
+                if (v == STAGE_ABORT) ok = false;
+                return v != STAGE_ABORT && v >= sidx;
+            };
+            bool passed = (si == 0) || (lane == 0 && is_open());
+            passed = __shfl_sync(0xffffffffu, (int)passed, 0) != 0;
             if (passed && si > 0) fence_proxy_async_global();  // before any TMA read of this stage
             uint32_t cur = stack_slot(a, st, u0 + lane, u1), nxt = stack_slot(a, st, u0 + 32 + lane, u1);
             for (uint64_t u = u0; u < u1; ++u, ++it) {
@@ -274,15 +297,17 @@ __global__ void __launch_bounds__(192, 1)
                         // a slot of the previous stage frees without the barrier;
                         // one of this stage's needs it: poll both
                         const unsigned long long t0 = globaltimer();
-                        while (ok && !mbar_try_wait(&empty[s], ph ^ 1)) {
-                            if (!passed && ld_acquire(a.bar) >= target) {
+                        for (uint32_t spin = 0; ok && !mbar_try_wait(&empty[s], ph ^ 1); ++spin) {
+                            if (!passed && is_open()) {
                                 passed = true;
                                 flush();
                             }
-                            if (aborted(a.abort)) ok = false;
-                            else if (globaltimer() - t0 > WAIT_LIMIT_NS) {
-                                give_up(a);
-                                ok = false;
+                            if ((spin & 63u) == 63u) {
+                                if (aborted(a.abort)) ok = false;
+                                else if (globaltimer() - t0 > WAIT_LIMIT_NS) {
+                                    give_up(a);
+                                    ok = false;
+                                }
                             }
                         }
                     }
@@ -295,7 +320,7 @@ __global__ void __launch_bounds__(192, 1)
                         tma_load_2d_hint(sa, &tw, &full[s], 0, row, pol_w);
                         tma_load_2d_hint(sa + 16384, &tw, &full[s], 64, row, pol_w);
                         const int32_t kc = (int32_t)(l.kt / (uint32_t)P.xratio) * 128;
-                        if (!passed && ld_acquire(a.bar) >= target) {
+                        if (!passed && is_open()) {
                             passed = true;
                             flush();
                         }
@@ -315,7 +340,17 @@ __global__ void __launch_bounds__(192, 1)
                 if (!ok) break;
             }
             if (lane == 0 && ok && !passed) {
-                ok = grid_wait(a, target);
+                const unsigned long long t0 = globaltimer();
+                for (uint32_t spin = 0; ok && !is_open(); ++spin) {
+                    __nanosleep(32);
+                    if ((spin & 63u) == 63u) {
+                        if (aborted(a.abort)) ok = false;
+                        else if (globaltimer() - t0 > WAIT_LIMIT_NS) {
+                            give_up(a);
+                            ok = false;
+                        }
+                    }
+                }
                 if (ok) flush();
             }
             ok = __shfl_sync(0xffffffffu, (int)ok, 0) != 0;
@@ -390,7 +425,11 @@ __global__ void __launch_bounds__(192, 1)
             const uint64_t u0 = blockIdx.x * T / G, u1 = (blockIdx.x + 1) * T / G;
             // inputs of this stage are complete once every CTA has arrived
             if (si > 0) {
-                if (et == 0) *last_flag = grid_wait(a, (uint32_t)(si * G)) ? 1u : 0u;
+                if (et == 0) {
+                    const bool pass = grid_wait(a, (uint32_t)(si * G));
+                    *last_flag = pass ? 1u : 0u;
+                    st_release_cta(stage_open, pass ? (uint32_t)si : STAGE_ABORT);
+                }
                 asm volatile("bar.sync 1, 128;" ::: "memory");
                 if (!*last_flag) { ok = false; break; }
             }
@@ -494,6 +533,7 @@ __global__ void __launch_bounds__(192, 1)
                             float ag[16], au[16];
 #pragma unroll
                             for (int j = 0; j < 16; ++j) ag[j] = au[j] = 0.0f;
+                            const bool paired = P.mode == MODE_SWIGLU;  // 'up' halves only when paired
                             for (uint32_t cb = c_first; cb <= c_last; cb += 4) {
                                 // all loads of up to four pieces in flight, then the
                                 // sums in CTA order
@@ -509,7 +549,8 @@ __global__ void __launch_bounds__(192, 1)
 #pragma unroll
                                     for (int j = 0; j < 4; ++j) {
                                         vg4[q][j] = __ldcg(reinterpret_cast<const float4 *>(pp) + j);
-                                        vu4[q][j] = __ldcg(reinterpret_cast<const float4 *>(pp + 128 * NPAD) + j);
+                                        vu4[q][j] = paired ? __ldcg(reinterpret_cast<const float4 *>(pp + 128 * NPAD) + j)
+                                                           : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
                                     }
                                 }
 #pragma unroll

@@ -157,7 +157,7 @@ static std::string stack_key(const cloak_stack_desc *d, int M) {
            std::to_string(d->d_ff) + " m" + std::to_string(m_bucket(M));
 }
 
-constexpr int STACK_L2PF_DEFAULT = 16;
+constexpr int STACK_L2PF_DEFAULT = 0;
 
 int stack_l2_prefetch(const cloak_ctx *ctx, const cloak_stack_desc *d, int M) {
     if (ctx->stack_l2_pf_force >= 0) return ctx->stack_l2_pf_force;
