@@ -31,6 +31,9 @@
 namespace cloak {
 
 enum { MODE_SCALED = 0, MODE_RESID = 1, MODE_SWIGLU = 2 };
+// tokens per accumulator row in the piece buffer, whatever the batch: a word's
+// address always means the same (CTA, gate/up, row, token)
+constexpr int PSTRIDE = 64;
 enum { XMAP_H = 0, XMAP_V = 1, XMAP_ACT = 2 };
 
 struct StackProb {
@@ -41,7 +44,6 @@ struct StackProb {
     int xmap, xratio;     // activation buffer; x tile = kt / xratio (o projection)
     int mode;
     __nv_bfloat16 *out;   // SCALED / SWIGLU output (bf16 [M, N])
-    uint32_t *rowcnt;     // arrival counters, one per tile row
 };
 
 struct StackStage {
@@ -59,7 +61,8 @@ struct StackArgs {
     int l2_pf;                // next-stage tiles per CTA prefetched into L2 (0: none)
     float *h;                 // FP32 residual [M, D]
     __nv_bfloat16 *hb;        // its BF16 copy (the activation operand)
-    float *part;              // [grid][2][2][128][NPAD]
+    unsigned long long *part; // [grid][2][128][PSTRIDE] tagged partial sums (gate, up)
+    const uint32_t *epoch;    // tag of this launch (advanced by k_stack_input)
     float *ss_rows;           // [D/128][64]: per residual row tile, its sum of squares per token
     const float *ss_init;     // [64]: sum of squares of the input residual
     unsigned int *bar;        // grid barrier arrivals (zeroed before launch)
@@ -201,6 +204,123 @@ __device__ __forceinline__ void tile_squares(float (&hsq)[16], int c0, int qd, i
     asm volatile("bar.sync 1, 128;" ::: "memory");
 }
 
+// Tagged partial sums: one 64-bit word per value, the launch tag in the high
+// half and the FP32 bits in the low half. A word is single-copy atomic, so a
+// reader that sees the current tag also sees the value written with it.
+__device__ __forceinline__ void st_tagged2(unsigned long long *p, float x, float y, uint32_t tag) {
+    const unsigned long long hi = (unsigned long long)tag << 32;
+    asm volatile("st.global.cg.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(hi | __float_as_uint(x)),
+                 "l"(hi | __float_as_uint(y))
+                 : "memory");
+}
+__device__ __forceinline__ void ld_tagged2(const unsigned long long *p, unsigned long long &x,
+                                           unsigned long long &y) {
+    asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(x), "=l"(y) : "l"(p));
+}
+__device__ __forceinline__ void clear_tagged2(unsigned long long *p) {
+    asm volatile("st.global.cg.v2.u64 [%0], {%1, %1};" ::"l"(p), "l"(0ull) : "memory");
+}
+__device__ __forceinline__ bool tags_are(unsigned long long x, unsigned long long y, uint32_t tag) {
+    return (uint32_t)(x >> 32) == tag && (uint32_t)(y >> 32) == tag;
+}
+// Reload a pair of words until both carry the tag (bounded like every wait of
+// the kernel; on giving up the values are left as they are).
+__device__ __forceinline__ void await_tagged2(const StackArgs &a, const unsigned long long *p,
+                                              unsigned long long &x, unsigned long long &y,
+                                              uint32_t tag) {
+    if (tags_are(x, y, tag)) return;
+    const unsigned long long t0 = globaltimer();
+    do {
+        ld_tagged2(p, x, y);
+        if (aborted(a.abort)) return;
+        if (globaltimer() - t0 > WAIT_LIMIT_NS) {
+            give_up(a);
+            return;
+        }
+    } while (!tags_are(x, y, tag));
+}
+
+// The finaliser of a split tile row adds, in CTA order, the pieces that the
+// CTAs after it hold of the row, for columns c0 .. c0+ncol-1 of this thread's
+// accumulator row (r_in). u1 is the end of this CTA's range, where the next
+// piece begins; re is the end of the row. Loads of up to IB (piece, four
+// columns) items are in flight at once; each word is cleared once taken.
+template <int NPAD, bool PAIRED>
+__device__ __forceinline__ void add_pieces(const StackArgs &a, float (&vg)[16], float (&vu)[16],
+                                           uint64_t u1, uint64_t re, uint64_t T, int c0, int ncol,
+                                           int r_in, uint32_t tag) {
+    constexpr int IB = PAIRED ? 4 : 8;
+    const uint64_t G = gridDim.x;
+    const int ng = (ncol + 3) >> 2;  // four-column groups of the chunk
+    int q_have = -1;                  // piece whose CTA is in 'cta'
+    uint32_t cta = 0;
+    uint64_t v = u1;                  // first unit of piece q_have + 1
+    int total = -1;                   // items of the row, once the walk has ended
+    for (int base = 0;; base += IB) {
+        unsigned long long eg[IB][4], eu[IB][4];
+        uint32_t pcta[IB];
+        int grp[IB];
+#pragma unroll
+        for (int k = 0; k < IB; ++k) {
+            const int item = base + k;
+            const int q = item / ng, g = item - q * ng;
+            if (q > q_have && total < 0) {
+                if (v < re) {
+                    cta = cta_of_unit(v, G, T);
+                    v = ((uint64_t)cta + 1) * T / G;
+                    q_have = q;
+                } else {
+                    total = q * ng;
+                }
+            }
+            const bool valid = q == q_have && (total < 0 || item < total);
+            grp[k] = valid ? g : -1;
+            pcta[k] = cta;
+            const unsigned long long *pk = a.part + ((uint64_t)cta * 2 * 128 + r_in) * PSTRIDE + c0 + 4 * g;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) eg[k][e] = eu[k][e] = 0ull;
+            if (valid) {
+                ld_tagged2(pk, eg[k][0], eg[k][1]);
+                if (4 * g + 2 < ncol) ld_tagged2(pk + 2, eg[k][2], eg[k][3]);
+                if (PAIRED) {
+                    ld_tagged2(pk + 128 * PSTRIDE, eu[k][0], eu[k][1]);
+                    if (4 * g + 2 < ncol) ld_tagged2(pk + 128 * PSTRIDE + 2, eu[k][2], eu[k][3]);
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < IB; ++k) {
+            const int g = grp[k];
+            if (g < 0) continue;
+            const bool two = 4 * g + 2 < ncol;
+            unsigned long long *pk = a.part + ((uint64_t)pcta[k] * 2 * 128 + r_in) * PSTRIDE + c0 + 4 * g;
+            await_tagged2(a, pk, eg[k][0], eg[k][1], tag);
+            if (two) await_tagged2(a, pk + 2, eg[k][2], eg[k][3], tag);
+            if (PAIRED) {
+                await_tagged2(a, pk + 128 * PSTRIDE, eu[k][0], eu[k][1], tag);
+                if (two) await_tagged2(a, pk + 128 * PSTRIDE + 2, eu[k][2], eu[k][3], tag);
+            }
+#pragma unroll
+            for (int gg = 0; gg < 4; ++gg) {
+                if (gg != g) continue;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    if (4 * gg + e >= ncol) continue;
+                    vg[4 * gg + e] += __uint_as_float((uint32_t)eg[k][e]);
+                    if (PAIRED) vu[4 * gg + e] += __uint_as_float((uint32_t)eu[k][e]);
+                }
+            }
+            clear_tagged2(pk);
+            if (two) clear_tagged2(pk + 2);
+            if (PAIRED) {
+                clear_tagged2(pk + 128 * PSTRIDE);
+                if (two) clear_tagged2(pk + 128 * PSTRIDE + 2);
+            }
+        }
+        if (total >= 0 && base + IB >= total) break;
+    }
+}
+
 template <int NPAD>
 __global__ void __launch_bounds__(192, 1)
     k_stack_tc(const __grid_constant__ CUtensorMap tw, const __grid_constant__ StackMaps xm,
@@ -216,6 +336,7 @@ __global__ void __launch_bounds__(192, 1)
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tempty + 2);
     volatile uint32_t *last_flag = tmem_slot + 1;
     uint32_t *stage_open = tmem_slot + 2;  // highest stage whose inputs are complete
+    volatile uint32_t *ok_flag = tmem_slot + 3;  // end of a stage: no CTA gave up
     float *rstd = reinterpret_cast<float *>(tmem_slot + 4);  // [NPAD]
     float *ss_w = rstd + 64;                                   // [4][16] per-warp chunk sums
 
@@ -414,9 +535,21 @@ __global__ void __launch_bounds__(192, 1)
         }
     } else {
         // ------------------------------------------------------- epilogue
+        // Warps 2..5 drain TMEM (lane quarter = warp % 4): one accumulator row
+        // per thread. A tile row split over CTAs is summed by the CTA holding
+        // its first tiles ("the finaliser"): that CTA reaches the row at the
+        // end of its range, the other CTAs at the start of theirs, so their
+        // pieces are written long before it needs them. A piece is stored as
+        // tagged words (launch epoch, value bits); the finaliser takes a word
+        // once its tag is the current epoch and clears it, so neither a flag
+        // nor a counter sits between the last tile and the row's output. The
+        // sum runs in CTA order (the finaliser's own piece first), whatever
+        // the timing, so results are deterministic and the cloaked and
+        // uncloaked kernels agree bit for bit.
         const int qd = warp & 3;
         const int r_in = qd * 32 + lane;
         const int et = threadIdx.x - 64;
+        const uint32_t tag = *a.epoch;
         uint32_t seg = 0;
         bool ok = true;
         for (int si = 0; si < a.nstages && ok; ++si) {
@@ -450,35 +583,64 @@ __global__ void __launch_bounds__(192, 1)
                 }
                 asm volatile("bar.sync 1, 128;" ::: "memory");
             }
-            const SLoc first = (u0 < u1) ? sloc(st, u0) : SLoc{0, 0, 0, 0, 0};
             for (uint64_t u = u0; u < u1; ++seg) {
                 const SLoc l = sloc(st, u);
                 const StackProb &P = st.p[l.p];
                 const uint64_t rs = l.row_begin, re = rs + P.upr;
                 const uint64_t send = umin64(u1, re);
-                const bool full_row = (u == rs) && (send == re);
                 const bool paired = P.mode == MODE_SWIGLU;
                 // which accumulators this piece wrote
                 const bool has_g = !paired || (send - u >= 2) || (((u - rs) & 1) == 0);
                 const bool has_u = paired && ((send - u >= 2) || (((u - rs) & 1) == 1));
+                const bool starts = u == rs;           // the row begins here: write its outputs
                 const uint32_t bf = seg & 1, use = seg >> 1;
-                if (!bar_wait(a, &tfull[bf], use & 1)) { ok = false; break; }
+                bar_wait(a, &tfull[bf], use & 1);      // a timeout sets the abort word
                 tc_fence_after();
                 const int row = (int)(l.nt * 128) + r_in;
                 const uint32_t tbase = tmem + ((uint32_t)(qd * 32) << 16) + bf * 2 * NPAD;
-                const int pslot = (l.p == first.p && l.nt == first.nt) ? 0 : 1;
-                float *mypart = a.part + ((((uint64_t)blockIdx.x * 2 + pslot) * 2) * 128 + r_in) * NPAD;
+                if (!starts) {
+                    // head piece of a row begun by an earlier CTA
+                    unsigned long long *pg = a.part + ((uint64_t)blockIdx.x * 2 * 128 + r_in) * PSTRIDE;
 #pragma unroll 1
-                for (int c0 = 0; c0 < NPAD; c0 += 16) {
-                    float vg[16], vu[16];
-                    tmem_ld16(tbase + c0, vg);
-                    tmem_ld16(tbase + NPAD + c0, vu);
+                    for (int c0 = 0; c0 < a.M; c0 += 16) {
+                        float vg[16], vu[16];
+                        tmem_ld16(tbase + c0, vg);
+                        if (paired) tmem_ld16(tbase + NPAD + c0, vu);
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        if (!has_g) vg[j] = 0.0f;
-                        if (!has_u) vu[j] = 0.0f;
+                        for (int j = 0; j < 16; j += 2) {
+                            if (c0 + j >= a.M) break;
+                            st_tagged2(pg + c0 + j, has_g ? vg[j] : 0.0f, has_g ? vg[j + 1] : 0.0f, tag);
+                            if (paired)
+                                st_tagged2(pg + 128 * PSTRIDE + c0 + j, has_u ? vu[j] : 0.0f,
+                                           has_u ? vu[j + 1] : 0.0f, tag);
+                        }
                     }
-                    if (full_row) {
+                    tc_fence_before();
+                    mbar_arrive(&tempty[bf]);
+                } else {
+                    const bool fin = send < re;        // later CTAs hold pieces of the row
+#pragma unroll 1
+                    for (int c0 = 0; c0 < a.M; c0 += 16) {
+                        const int ncol = min(16, a.M - c0);
+                        float hv[16];
+                        if (P.mode == MODE_RESID) {
+                            // the residual's old values, in flight with the pieces
+#pragma unroll
+                            for (int j = 0; j < 16; ++j)
+                                hv[j] = (j < ncol && row < P.N) ? a.h[(size_t)(c0 + j) * P.N + row] : 0.0f;
+                        }
+                        float vg[16], vu[16];
+                        tmem_ld16(tbase + c0, vg);
+                        if (paired) tmem_ld16(tbase + NPAD + c0, vu);
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            if (!has_g) vg[j] = 0.0f;
+                            if (!paired || !has_u) vu[j] = 0.0f;
+                        }
+                        if (fin) {
+                            if (paired) add_pieces<NPAD, true>(a, vg, vu, u1, re, T, c0, ncol, r_in, tag);
+                            else add_pieces<NPAD, false>(a, vg, vu, u1, re, T, c0, ncol, r_in, tag);
+                        }
                         float hsq[16];
 #pragma unroll
                         for (int j = 0; j < 16; ++j) hsq[j] = 0.0f;
@@ -486,12 +648,12 @@ __global__ void __launch_bounds__(192, 1)
 #pragma unroll
                             for (int j = 0; j < 16; ++j) {
                                 const int m = c0 + j;
-                                if (m >= a.M) continue;
+                                if (j >= ncol) continue;
                                 const size_t o = (size_t)m * P.N + row;
                                 if (P.mode == MODE_SCALED) {
                                     P.out[o] = __float2bfloat16_rn(vg[j] * rstd[m]);
                                 } else if (P.mode == MODE_RESID) {
-                                    const float hn = a.h[o] + vg[j];
+                                    const float hn = hv[j] + vg[j];
                                     a.h[o] = hn;
                                     a.hb[o] = __float2bfloat16_rn(hn);
                                     hsq[j] = hn * hn;
@@ -501,95 +663,9 @@ __global__ void __launch_bounds__(192, 1)
                             }
                         }
                         if (P.mode == MODE_RESID) tile_squares(hsq, c0, qd, lane, et, ss_w, a.ss_rows + (size_t)l.nt * 64);
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < 16; j += 4) {
-                            __stcg(reinterpret_cast<float4 *>(mypart + c0 + j),
-                                   make_float4(vg[j], vg[j + 1], vg[j + 2], vg[j + 3]));
-                            __stcg(reinterpret_cast<float4 *>(mypart + 128 * NPAD + c0 + j),
-                                   make_float4(vu[j], vu[j + 1], vu[j + 2], vu[j + 3]));
-                        }
                     }
-                }
-                tc_fence_before();
-                mbar_arrive(&tempty[bf]);
-                if (!full_row) {
-                    asm volatile("bar.sync 1, 128;" ::: "memory");
-                    const uint32_t c_first = cta_of_unit(rs, G, T), c_last = cta_of_unit(re - 1, G, T);
-                    if (et == 0) {
-                        // CTAs in [c_first, c_last] with an empty range (a stage
-                        // with fewer units than CTAs) hold no piece of the row
-                        uint32_t pieces = 0;
-                        for (uint32_t c = c_first; c <= c_last; ++c)
-                            pieces += ((uint64_t)c * T / G < ((uint64_t)c + 1) * T / G) ? 1u : 0u;
-                        const uint32_t old = atom_add_acq_rel(P.rowcnt + l.nt, 1u);
-                        *last_flag = (old == pieces - 1) ? 1u : 0u;
-                    }
-                    asm volatile("bar.sync 1, 128;" ::: "memory");
-                    if (*last_flag) {
-                        const int ps_first = ((uint64_t)c_first * T / G < rs) ? 1 : 0;
-#pragma unroll 1
-                        for (int c0 = 0; c0 < NPAD; c0 += 16) {
-                            float ag[16], au[16];
-#pragma unroll
-                            for (int j = 0; j < 16; ++j) ag[j] = au[j] = 0.0f;
-                            const bool paired = P.mode == MODE_SWIGLU;  // 'up' halves only when paired
-                            for (uint32_t cb = c_first; cb <= c_last; cb += 4) {
-                                // all loads of up to four pieces in flight, then the
-                                // sums in CTA order
-                                float4 vg4[4][4], vu4[4][4];
-                                bool has[4];
-#pragma unroll
-                                for (int q = 0; q < 4; ++q) {
-                                    const uint32_t c = cb + q;
-                                    has[q] = c <= c_last && ((uint64_t)c * T / G < ((uint64_t)c + 1) * T / G);
-                                    if (!has[q]) continue;
-                                    const int ps = (c == c_first) ? ps_first : 0;
-                                    const float *pp = a.part + ((((uint64_t)c * 2 + ps) * 2) * 128 + r_in) * NPAD + c0;
-#pragma unroll
-                                    for (int j = 0; j < 4; ++j) {
-                                        vg4[q][j] = __ldcg(reinterpret_cast<const float4 *>(pp) + j);
-                                        vu4[q][j] = paired ? __ldcg(reinterpret_cast<const float4 *>(pp + 128 * NPAD) + j)
-                                                           : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-                                    }
-                                }
-#pragma unroll
-                                for (int q = 0; q < 4; ++q) {
-                                    if (!has[q]) continue;
-#pragma unroll
-                                    for (int j = 0; j < 4; ++j) {
-                                        ag[4 * j] += vg4[q][j].x; ag[4 * j + 1] += vg4[q][j].y;
-                                        ag[4 * j + 2] += vg4[q][j].z; ag[4 * j + 3] += vg4[q][j].w;
-                                        au[4 * j] += vu4[q][j].x; au[4 * j + 1] += vu4[q][j].y;
-                                        au[4 * j + 2] += vu4[q][j].z; au[4 * j + 3] += vu4[q][j].w;
-                                    }
-                                }
-                            }
-                            float hsq[16];
-#pragma unroll
-                            for (int j = 0; j < 16; ++j) hsq[j] = 0.0f;
-                            if (row < P.N) {
-#pragma unroll
-                                for (int j = 0; j < 16; ++j) {
-                                    const int m = c0 + j;
-                                    if (m >= a.M) continue;
-                                    const size_t o = (size_t)m * P.N + row;
-                                    if (P.mode == MODE_SCALED) {
-                                        P.out[o] = __float2bfloat16_rn(ag[j] * rstd[m]);
-                                    } else if (P.mode == MODE_RESID) {
-                                        const float hn = a.h[o] + ag[j];
-                                        a.h[o] = hn;
-                                        a.hb[o] = __float2bfloat16_rn(hn);
-                                        hsq[j] = hn * hn;
-                                    } else {
-                                        P.out[o] = __float2bfloat16_rn(silu(ag[j] * rstd[m]) * (au[j] * rstd[m]));
-                                    }
-                                }
-                            }
-                            if (P.mode == MODE_RESID) tile_squares(hsq, c0, qd, lane, et, ss_w, a.ss_rows + (size_t)l.nt * 64);
-                        }
-                        if (et == 0) P.rowcnt[l.nt] = 0;
-                    }
+                    tc_fence_before();
+                    mbar_arrive(&tempty[bf]);
                 }
                 u = send;
             }
@@ -602,8 +678,10 @@ __global__ void __launch_bounds__(192, 1)
             if (et == 0) {
                 __threadfence();
                 atomicAdd(a.bar, 1u);
+                *ok_flag = aborted(a.abort) ? 0u : 1u;
             }
-            if (aborted(a.abort)) ok = false;
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            if (!*ok_flag) ok = false;  // the same decision in every epilogue thread
         }
     }
     tc_fence_before();
@@ -616,9 +694,15 @@ __global__ void __launch_bounds__(192, 1)
 
 // --------------------------------------------------------------------- host
 
-// BF16 copy of the input residual and its per-token sum of squares
-__global__ void k_stack_input(const float *h, int D, __nv_bfloat16 *hb, float *ss) {
+// BF16 copy of the input residual and its per-token sum of squares; advances
+// the launch tag of the stack kernel that follows (0 is never a tag: the
+// workspace starts zeroed)
+__global__ void k_stack_input(const float *h, int D, __nv_bfloat16 *hb, float *ss, uint32_t *epoch) {
     const int m = blockIdx.x;
+    if (m == 0 && threadIdx.x == 0) {
+        const uint32_t e = *epoch + 1u;
+        *epoch = e ? e : 1u;
+    }
     float acc = 0.0f;
     for (int c = threadIdx.x; c < D; c += blockDim.x) {
         const float v = h[(size_t)m * D + c];
@@ -690,39 +774,40 @@ cloak_status stack_decode_run(cloak_ctx *ctx, const cloak_stack_desc *d, float *
     const int G = ctx->sm_count;
     // workspace: bf16 activations, partial sums, counters, barrier
     const size_t act_elems = (size_t)M * (D + HQ + 2 * HKV + F);
-    const size_t part_floats = (size_t)G * 2 * 2 * 128 * npad;
+    const size_t part_words = (size_t)G * 2 * 128 * PSTRIDE;  // tagged 64-bit words
     const size_t nstages = 4 * (size_t)d->num_layers;
-    size_t rows = 0;
-    for (int l = 0; l < d->num_layers; ++l)
-        for (int j = 0; j < 7; ++j) rows += ctx->info[d->layer_tensors[l * 7 + j]].nt;
     auto r256 = [](size_t n) { return (n + 255) & ~(size_t)255; };
     const size_t bytes = r256((size_t)M * D * 2) + r256((size_t)M * HQ * 2) + 2 * r256((size_t)M * HKV * 2) +
-                         r256((size_t)M * F * 2) + r256(part_floats * 4) + r256(rows * 4) + r256(8) +
+                         r256((size_t)M * F * 2) + r256(part_words * 8) + r256(16) +
                          r256(nstages * sizeof(StackStage)) + r256((size_t)(D / 128 + 1) * 64 * 4);
     (void)act_elems;
     cudaError_t err = cudaSuccess;
     void *before = ctx->d_stack_ws;
     uint8_t *w = (uint8_t *)grow(ctx, ctx->d_stack_ws, ctx->stack_ws_cap, bytes, err);
-    if (ctx->d_stack_ws != before) ctx->stack_sig.clear();
     if (err != cudaSuccess) return cuda_fail(ctx, err, "stack workspace");
+    if (ctx->d_stack_ws != before) {
+        // a fresh workspace holds no valid tag (and the launch epoch starts at 0)
+        ctx->stack_sig.clear();
+        CLOAK_CUDA(ctx, cudaMemsetAsync(ctx->d_stack_ws, 0, ctx->stack_ws_cap, s));
+    }
     auto take = [&](size_t n) {
         uint8_t *p = w;
         w += (n + 255) & ~(size_t)255;
         return p;
     };
+    // fixed offsets first: the launch epoch and the piece buffer only ever hold
+    // their own contents, so no stale word can carry a current tag
+    uint32_t *bar = (uint32_t *)take(16);  // [0] barrier arrivals, [1] abort, [2] launch epoch
+    unsigned long long *part = (unsigned long long *)take(part_words * 8);
     __nv_bfloat16 *hb = (__nv_bfloat16 *)take((size_t)M * D * 2);
     __nv_bfloat16 *qb = (__nv_bfloat16 *)take((size_t)M * HQ * 2);
     __nv_bfloat16 *kb = (__nv_bfloat16 *)take((size_t)M * HKV * 2);
     __nv_bfloat16 *vb = (__nv_bfloat16 *)take((size_t)M * HKV * 2);
     __nv_bfloat16 *ab = (__nv_bfloat16 *)take((size_t)M * F * 2);
-    float *part = (float *)take(part_floats * 4);
-    uint32_t *cnt = (uint32_t *)take(rows * 4);
-    uint32_t *bar = (uint32_t *)take(8);
     StackStage *dst = (StackStage *)take(nstages * sizeof(StackStage));
     float *ss = (float *)take((size_t)(D / 128 + 1) * 64 * 4);  // [D/128][64] row tiles, then [64] input
     // the stage program
     std::vector<StackStage> st(nstages);
-    size_t roff = 0;
     auto prob = [&](StackProb &P, int t, int t2, int xmap, int xratio, int mode, __nv_bfloat16 *out,
                     uint64_t u_begin) {
         const TensorInfo &ti = ctx->info[t];
@@ -737,8 +822,6 @@ cloak_status stack_decode_run(cloak_ctx *ctx, const cloak_stack_desc *d, float *
         P.xratio = xratio;
         P.mode = mode;
         P.out = out;
-        P.rowcnt = cnt + roff;
-        roff += ti.nt;
         return (uint64_t)ti.nt * P.upr;
     };
     for (int l = 0; l < d->num_layers; ++l) {
@@ -758,9 +841,7 @@ cloak_status stack_decode_run(cloak_ctx *ctx, const cloak_stack_desc *d, float *
         Cs = StackStage{};
         Cs.np = 1;
         Cs.need_rstd = 1;
-        roff += 0;
         Cs.total = prob(Cs.p[0], lt[4], lt[5], XMAP_H, 1, MODE_SWIGLU, ab, 0);
-        roff += ctx->info[lt[5]].nt;  // counters of the paired tensor are unused; keep layout simple
         Dd = StackStage{};
         Dd.np = 1;
         Dd.total = prob(Dd.p[0], lt[6], -1, XMAP_ACT, 1, MODE_RESID, nullptr, 0);
@@ -775,9 +856,8 @@ cloak_status stack_decode_run(cloak_ctx *ctx, const cloak_stack_desc *d, float *
         CLOAK_CUDA(ctx, cudaStreamSynchronize(s));
         ctx->stack_sig.swap(sig);
     }
-    CLOAK_CUDA(ctx, cudaMemsetAsync(cnt, 0, rows * 4, s));
     CLOAK_CUDA(ctx, cudaMemsetAsync(bar, 0, 8, s));
-    k_stack_input<<<M, 256, 0, s>>>(h, D, hb, ss + (size_t)(D / 128) * 64);
+    k_stack_input<<<M, 256, 0, s>>>(h, D, hb, ss + (size_t)(D / 128) * 64, bar + 2);
     CLOAK_LAUNCHED(ctx);
     StackMaps xm;
     if (!encode_tmap_2d(&xm.m[XMAP_H], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, hb, D, M, (uint64_t)D * 2, 64, npad) ||
@@ -798,6 +878,7 @@ cloak_status stack_decode_run(cloak_ctx *ctx, const cloak_stack_desc *d, float *
     a.h = h;
     a.hb = hb;
     a.part = part;
+    a.epoch = bar + 2;
     a.ss_rows = ss;
     a.ss_init = ss + (size_t)(D / 128) * 64;
     a.bar = bar;
