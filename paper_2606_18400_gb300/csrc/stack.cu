@@ -31,9 +31,13 @@
 namespace cloak {
 
 enum { MODE_SCALED = 0, MODE_RESID = 1, MODE_SWIGLU = 2 };
-// tokens per accumulator row in the piece buffer, whatever the batch: a word's
-// address always means the same (CTA, gate/up, row, token)
-constexpr int PSTRIDE = 64;
+// Split tile rows are summed in one of two ways. Up to 16 tokens: by the CTA
+// holding the row's first tiles, from tagged words (below). Wider batches: by
+// the CTA that arrives last on the row's counter, from FP32 pieces; there the
+// finaliser's reads, not the hand-off, dominate, and plain floats halve them.
+// Tokens per accumulator row in the tagged buffer, whatever the batch: a
+// word's address always means the same (CTA, gate/up, row, token).
+constexpr int PSTRIDE = 16;
 enum { XMAP_H = 0, XMAP_V = 1, XMAP_ACT = 2 };
 
 struct StackProb {
@@ -44,6 +48,7 @@ struct StackProb {
     int xmap, xratio;     // activation buffer; x tile = kt / xratio (o projection)
     int mode;
     __nv_bfloat16 *out;   // SCALED / SWIGLU output (bf16 [M, N])
+    uint32_t *rowcnt;     // arrival counters, one per tile row (batches over 16)
 };
 
 struct StackStage {
@@ -61,7 +66,8 @@ struct StackArgs {
     int l2_pf;                // next-stage tiles per CTA prefetched into L2 (0: none)
     float *h;                 // FP32 residual [M, D]
     __nv_bfloat16 *hb;        // its BF16 copy (the activation operand)
-    unsigned long long *part; // [grid][2][128][PSTRIDE] tagged partial sums (gate, up)
+    unsigned long long *part; // [grid][2 gate/up][128][PSTRIDE] tagged partial sums (M <= 16)
+    float *partf;             // [grid][2 pieces][2 gate/up][128][NPAD] partial sums (M > 16)
     const uint32_t *epoch;    // tag of this launch (advanced by k_stack_input)
     float *ss_rows;           // [D/128][64]: per residual row tile, its sum of squares per token
     const float *ss_init;     // [64]: sum of squares of the input residual
@@ -186,11 +192,11 @@ __device__ __forceinline__ void st_release_cta(uint32_t *p, uint32_t v) {
 
 __device__ __forceinline__ float silu(float g) { return g / (1.0f + expf(-g)); }
 
-// Sum of squares of a finalised residual row tile for tokens c0..c0+15
+// Sum of squares of a finalised residual row tile for tokens c0..c0+ncol-1
 // (hsq[j]: this thread's row, 0 where it wrote nothing): warp sums, then the
-// four warps in fixed order, stored for the tile. Each tile has one
-// finaliser per stage, so the result does not depend on which CTA it is.
-__device__ __forceinline__ void tile_squares(float (&hsq)[16], int c0, int qd, int lane, int et,
+// four warps in fixed order, stored for the tile. Each (tile, token) has one
+// writer per stage, so the result does not depend on which CTA it is.
+__device__ __forceinline__ void tile_squares(float (&hsq)[16], int c0, int ncol, int qd, int lane, int et,
                                              float *ss_w, float *dst) {
 #pragma unroll
     for (int j = 0; j < 16; ++j)
@@ -200,7 +206,7 @@ __device__ __forceinline__ void tile_squares(float (&hsq)[16], int c0, int qd, i
         for (int j = 0; j < 16; ++j) ss_w[qd * 16 + j] = hsq[j];
     }
     asm volatile("bar.sync 1, 128;" ::: "memory");
-    if (et < 16) dst[c0 + et] = ss_w[et] + ss_w[16 + et] + ss_w[32 + et] + ss_w[48 + et];
+    if (et < ncol) dst[c0 + et] = ss_w[et] + ss_w[16 + et] + ss_w[32 + et] + ss_w[48 + et];
     asm volatile("bar.sync 1, 128;" ::: "memory");
 }
 
@@ -240,21 +246,28 @@ __device__ __forceinline__ void await_tagged2(const StackArgs &a, const unsigned
     } while (!tags_are(x, y, tag));
 }
 
+// Word of the tagged piece buffer: CTA c's piece, gate or up accumulator,
+// accumulator row r, token m.
+__device__ __forceinline__ unsigned long long *piece_word(const StackArgs &a, uint32_t c, int up, int r, int m) {
+    return a.part + (((uint64_t)c * 2 + up) * 128 + r) * PSTRIDE + m;
+}
+
 // The finaliser of a split tile row adds, in CTA order, the pieces that the
-// CTAs after it hold of the row, for columns c0 .. c0+ncol-1 of this thread's
-// accumulator row (r_in). u1 is the end of this CTA's range, where the next
-// piece begins; re is the end of the row. Loads of up to IB (piece, four
-// columns) items are in flight at once; each word is cleared once taken.
+// CTAs after it hold of the row, for tokens c0 .. c0+ncol-1 (c0 even) of
+// this thread's accumulator row r_in. v0 is the end of this CTA's range, where
+// the next piece begins; re is the end of the row. Each such piece is the head
+// of its CTA's range. Loads of up to IB (piece, four tokens) items are in
+// flight at once; each word is cleared once taken.
 template <int NPAD, bool PAIRED>
 __device__ __forceinline__ void add_pieces(const StackArgs &a, float (&vg)[16], float (&vu)[16],
-                                           uint64_t u1, uint64_t re, uint64_t T, int c0, int ncol,
+                                           uint64_t v0, uint64_t re, uint64_t T, int c0, int ncol,
                                            int r_in, uint32_t tag) {
     constexpr int IB = PAIRED ? 4 : 8;
     const uint64_t G = gridDim.x;
-    const int ng = (ncol + 3) >> 2;  // four-column groups of the chunk
+    const int ng = (ncol + 3) >> 2;  // four-token groups of the chunk
     int q_have = -1;                  // piece whose CTA is in 'cta'
     uint32_t cta = 0;
-    uint64_t v = u1;                  // first unit of piece q_have + 1
+    uint64_t v = v0;                  // first unit of piece q_have + 1
     int total = -1;                   // items of the row, once the walk has ended
     for (int base = 0;; base += IB) {
         unsigned long long eg[IB][4], eu[IB][4];
@@ -276,15 +289,16 @@ __device__ __forceinline__ void add_pieces(const StackArgs &a, float (&vg)[16], 
             const bool valid = q == q_have && (total < 0 || item < total);
             grp[k] = valid ? g : -1;
             pcta[k] = cta;
-            const unsigned long long *pk = a.part + ((uint64_t)cta * 2 * 128 + r_in) * PSTRIDE + c0 + 4 * g;
+            const unsigned long long *pg = piece_word(a, cta, 0, r_in, c0 + 4 * g);
+            const unsigned long long *pu = piece_word(a, cta, 1, r_in, c0 + 4 * g);
 #pragma unroll
             for (int e = 0; e < 4; ++e) eg[k][e] = eu[k][e] = 0ull;
             if (valid) {
-                ld_tagged2(pk, eg[k][0], eg[k][1]);
-                if (4 * g + 2 < ncol) ld_tagged2(pk + 2, eg[k][2], eg[k][3]);
+                ld_tagged2(pg, eg[k][0], eg[k][1]);
+                if (4 * g + 2 < ncol) ld_tagged2(pg + 2, eg[k][2], eg[k][3]);
                 if (PAIRED) {
-                    ld_tagged2(pk + 128 * PSTRIDE, eu[k][0], eu[k][1]);
-                    if (4 * g + 2 < ncol) ld_tagged2(pk + 128 * PSTRIDE + 2, eu[k][2], eu[k][3]);
+                    ld_tagged2(pu, eu[k][0], eu[k][1]);
+                    if (4 * g + 2 < ncol) ld_tagged2(pu + 2, eu[k][2], eu[k][3]);
                 }
             }
         }
@@ -293,12 +307,13 @@ __device__ __forceinline__ void add_pieces(const StackArgs &a, float (&vg)[16], 
             const int g = grp[k];
             if (g < 0) continue;
             const bool two = 4 * g + 2 < ncol;
-            unsigned long long *pk = a.part + ((uint64_t)pcta[k] * 2 * 128 + r_in) * PSTRIDE + c0 + 4 * g;
-            await_tagged2(a, pk, eg[k][0], eg[k][1], tag);
-            if (two) await_tagged2(a, pk + 2, eg[k][2], eg[k][3], tag);
+            unsigned long long *pg = piece_word(a, pcta[k], 0, r_in, c0 + 4 * g);
+            unsigned long long *pu = piece_word(a, pcta[k], 1, r_in, c0 + 4 * g);
+            await_tagged2(a, pg, eg[k][0], eg[k][1], tag);
+            if (two) await_tagged2(a, pg + 2, eg[k][2], eg[k][3], tag);
             if (PAIRED) {
-                await_tagged2(a, pk + 128 * PSTRIDE, eu[k][0], eu[k][1], tag);
-                if (two) await_tagged2(a, pk + 128 * PSTRIDE + 2, eu[k][2], eu[k][3], tag);
+                await_tagged2(a, pu, eu[k][0], eu[k][1], tag);
+                if (two) await_tagged2(a, pu + 2, eu[k][2], eu[k][3], tag);
             }
 #pragma unroll
             for (int gg = 0; gg < 4; ++gg) {
@@ -310,15 +325,98 @@ __device__ __forceinline__ void add_pieces(const StackArgs &a, float (&vg)[16], 
                     if (PAIRED) vu[4 * gg + e] += __uint_as_float((uint32_t)eu[k][e]);
                 }
             }
-            clear_tagged2(pk);
-            if (two) clear_tagged2(pk + 2);
+            clear_tagged2(pg);
+            if (two) clear_tagged2(pg + 2);
             if (PAIRED) {
-                clear_tagged2(pk + 128 * PSTRIDE);
-                if (two) clear_tagged2(pk + 128 * PSTRIDE + 2);
+                clear_tagged2(pu);
+                if (two) clear_tagged2(pu + 2);
             }
         }
         if (total >= 0 && base + IB >= total) break;
     }
+}
+
+// Sum, in CTA order, the FP32 pieces that CTAs c_first..c_last hold of a
+// split row (c_first's in slot ps_first, the others' in slot 0), tokens
+// c0..c0+15 of accumulator row r_in; the loads of PB pieces are in flight at
+// once.
+template <int NPAD, bool PAIRED>
+__device__ __forceinline__ void sum_pieces(const StackArgs &a, float (&ag)[16], float (&au)[16], uint32_t c_first,
+                                           uint32_t c_last, int ps_first, uint64_t T, int r_in, int c0) {
+    constexpr int PB = 2;  // pieces whose loads are in flight at once
+    const uint64_t G = gridDim.x;
+    for (uint32_t cb = c_first; cb <= c_last; cb += PB) {
+        float4 vg4[PB][4], vu4[PB][4];
+        bool has[PB];
+#pragma unroll
+        for (int q = 0; q < PB; ++q) {
+            const uint32_t c = cb + q;
+            has[q] = c <= c_last && ((uint64_t)c * T / G < ((uint64_t)c + 1) * T / G);
+            if (!has[q]) continue;
+            const int ps = (c == c_first) ? ps_first : 0;
+            const float *pp = a.partf + ((((uint64_t)c * 2 + ps) * 2) * 128 + r_in) * NPAD + c0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                vg4[q][j] = __ldcg(reinterpret_cast<const float4 *>(pp) + j);
+                if (PAIRED) vu4[q][j] = __ldcg(reinterpret_cast<const float4 *>(pp + 128 * NPAD) + j);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < PB; ++q) {
+            if (!has[q]) continue;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                ag[4 * j] += vg4[q][j].x; ag[4 * j + 1] += vg4[q][j].y;
+                ag[4 * j + 2] += vg4[q][j].z; ag[4 * j + 3] += vg4[q][j].w;
+                if (PAIRED) {
+                    au[4 * j] += vu4[q][j].x; au[4 * j + 1] += vu4[q][j].y;
+                    au[4 * j + 2] += vu4[q][j].z; au[4 * j + 3] += vu4[q][j].w;
+                }
+            }
+        }
+    }
+}
+
+// Outputs of tokens c0 .. c0+ncol-1 of accumulator row r_in of tile row nt
+// (vg, vu: the row's sums; hv: the residual's old values): scaled store,
+// residual update with the tile's sums of squares, or SwiGLU.
+__device__ __forceinline__ void emit_chunk(const StackArgs &a, const StackProb &P, uint32_t nt, int c0,
+                                           int ncol, int r_in, const float (&vg)[16], const float (&vu)[16],
+                                           const float (&hv)[16], const float *rstd, int qd, int lane, int et,
+                                           float *ss_w) {
+    const int row = (int)(nt * 128) + r_in;
+    float hsq[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) hsq[j] = 0.0f;
+    if (row < P.N) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            if (j >= ncol) continue;
+            const int m = c0 + j;
+            const size_t o = (size_t)m * P.N + row;
+            if (P.mode == MODE_SCALED) {
+                P.out[o] = __float2bfloat16_rn(vg[j] * rstd[m]);
+            } else if (P.mode == MODE_RESID) {
+                const float hn = hv[j] + vg[j];
+                a.h[o] = hn;
+                a.hb[o] = __float2bfloat16_rn(hn);
+                hsq[j] = hn * hn;
+            } else {
+                P.out[o] = __float2bfloat16_rn(silu(vg[j] * rstd[m]) * (vu[j] * rstd[m]));
+            }
+        }
+    }
+    if (P.mode == MODE_RESID) tile_squares(hsq, c0, ncol, qd, lane, et, ss_w, a.ss_rows + (size_t)nt * 64);
+}
+
+// The residual's old values of tokens c0 .. c0+ncol-1 of tile row nt (zero
+// elsewhere), loaded ahead of the sums they are added to.
+__device__ __forceinline__ void load_resid(const StackArgs &a, const StackProb &P, uint32_t nt, int c0,
+                                           int ncol, int r_in, float (&hv)[16]) {
+    const int row = (int)(nt * 128) + r_in;
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+        hv[j] = (P.mode == MODE_RESID && j < ncol && row < P.N) ? a.h[(size_t)(c0 + j) * P.N + row] : 0.0f;
 }
 
 template <int NPAD>
@@ -583,53 +681,80 @@ __global__ void __launch_bounds__(192, 1)
                 }
                 asm volatile("bar.sync 1, 128;" ::: "memory");
             }
-            for (uint64_t u = u0; u < u1; ++seg) {
-                const SLoc l = sloc(st, u);
-                const StackProb &P = st.p[l.p];
-                const uint64_t rs = l.row_begin, re = rs + P.upr;
-                const uint64_t send = umin64(u1, re);
-                const bool paired = P.mode == MODE_SWIGLU;
-                // which accumulators this piece wrote
-                const bool has_g = !paired || (send - u >= 2) || (((u - rs) & 1) == 0);
-                const bool has_u = paired && ((send - u >= 2) || (((u - rs) & 1) == 1));
-                const bool starts = u == rs;           // the row begins here: write its outputs
-                const uint32_t bf = seg & 1, use = seg >> 1;
-                bar_wait(a, &tfull[bf], use & 1);      // a timeout sets the abort word
-                tc_fence_after();
-                const int row = (int)(l.nt * 128) + r_in;
-                const uint32_t tbase = tmem + ((uint32_t)(qd * 32) << 16) + bf * 2 * NPAD;
-                if (!starts) {
-                    // head piece of a row begun by an earlier CTA
-                    unsigned long long *pg = a.part + ((uint64_t)blockIdx.x * 2 * 128 + r_in) * PSTRIDE;
-#pragma unroll 1
-                    for (int c0 = 0; c0 < a.M; c0 += 16) {
+            if constexpr (NPAD == 16) {
+                for (uint64_t u = u0; u < u1; ++seg) {
+                    const SLoc l = sloc(st, u);
+                    const StackProb &P = st.p[l.p];
+                    const uint64_t rs = l.row_begin, re = rs + P.upr;
+                    const uint64_t send = umin64(u1, re);
+                    const bool paired = P.mode == MODE_SWIGLU;
+                    // which accumulators this piece wrote
+                    const bool has_g = !paired || (send - u >= 2) || (((u - rs) & 1) == 0);
+                    const bool has_u = paired && ((send - u >= 2) || (((u - rs) & 1) == 1));
+                    const uint32_t bf = seg & 1, use = seg >> 1;
+                    bar_wait(a, &tfull[bf], use & 1);  // a timeout sets the abort word
+                    tc_fence_after();
+                    const uint32_t tbase = tmem + ((uint32_t)(qd * 32) << 16) + bf * 2 * NPAD;
+                    if (u != rs) {
+                        // head piece of a row begun by an earlier CTA: tagged words
+                        unsigned long long *pg = piece_word(a, blockIdx.x, 0, r_in, 0);
+                        unsigned long long *pu = piece_word(a, blockIdx.x, 1, r_in, 0);
                         float vg[16], vu[16];
-                        tmem_ld16(tbase + c0, vg);
-                        if (paired) tmem_ld16(tbase + NPAD + c0, vu);
+                        tmem_ld16(tbase, vg);
+                        if (paired) tmem_ld16(tbase + NPAD, vu);
 #pragma unroll
                         for (int j = 0; j < 16; j += 2) {
-                            if (c0 + j >= a.M) break;
-                            st_tagged2(pg + c0 + j, has_g ? vg[j] : 0.0f, has_g ? vg[j + 1] : 0.0f, tag);
-                            if (paired)
-                                st_tagged2(pg + 128 * PSTRIDE + c0 + j, has_u ? vu[j] : 0.0f,
-                                           has_u ? vu[j + 1] : 0.0f, tag);
+                            if (j >= a.M) break;
+                            st_tagged2(pg + j, has_g ? vg[j] : 0.0f, has_g ? vg[j + 1] : 0.0f, tag);
+                            if (paired) st_tagged2(pu + j, has_u ? vu[j] : 0.0f, has_u ? vu[j + 1] : 0.0f, tag);
                         }
+                    } else {
+                        // the row begins here: a full row, or the finaliser's
+                        // own piece plus those of the CTAs after it
+                        float hv[16], vg[16], vu[16];
+                        load_resid(a, P, l.nt, 0, a.M, r_in, hv);
+                        tmem_ld16(tbase, vg);
+                        if (paired) tmem_ld16(tbase + NPAD, vu);
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            if (!has_g) vg[j] = 0.0f;
+                            if (!paired || !has_u) vu[j] = 0.0f;
+                        }
+                        if (send < re) {
+                            if (paired) add_pieces<NPAD, true>(a, vg, vu, u1, re, T, 0, a.M, r_in, tag);
+                            else add_pieces<NPAD, false>(a, vg, vu, u1, re, T, 0, a.M, r_in, tag);
+                        }
+                        emit_chunk(a, P, l.nt, 0, a.M, r_in, vg, vu, hv, rstd, qd, lane, et, ss_w);
                     }
                     tc_fence_before();
                     mbar_arrive(&tempty[bf]);
-                } else {
-                    const bool fin = send < re;        // later CTAs hold pieces of the row
+                    u = send;
+                }
+            } else {
+                // wider batches: pieces as FP32 in per-CTA slots (0: the first
+                // segment's row, 1: the last), summed in CTA order by the CTA
+                // that arrives last on the row's counter
+                const SLoc first = (u0 < u1) ? sloc(st, u0) : SLoc{0, 0, 0, 0, 0};
+                for (uint64_t u = u0; u < u1; ++seg) {
+                    const SLoc l = sloc(st, u);
+                    const StackProb &P = st.p[l.p];
+                    const uint64_t rs = l.row_begin, re = rs + P.upr;
+                    const uint64_t send = umin64(u1, re);
+                    const bool full_row = (u == rs) && (send == re);
+                    const bool paired = P.mode == MODE_SWIGLU;
+                    const bool has_g = !paired || (send - u >= 2) || (((u - rs) & 1) == 0);
+                    const bool has_u = paired && ((send - u >= 2) || (((u - rs) & 1) == 1));
+                    const uint32_t bf = seg & 1, use = seg >> 1;
+                    bar_wait(a, &tfull[bf], use & 1);  // a timeout sets the abort word
+                    tc_fence_after();
+                    const uint32_t tbase = tmem + ((uint32_t)(qd * 32) << 16) + bf * 2 * NPAD;
+                    const int pslot = (l.p == first.p && l.nt == first.nt) ? 0 : 1;
+                    float *mypart = a.partf + ((((uint64_t)blockIdx.x * 2 + pslot) * 2) * 128 + r_in) * NPAD;
 #pragma unroll 1
                     for (int c0 = 0; c0 < a.M; c0 += 16) {
                         const int ncol = min(16, a.M - c0);
-                        float hv[16];
-                        if (P.mode == MODE_RESID) {
-                            // the residual's old values, in flight with the pieces
-#pragma unroll
-                            for (int j = 0; j < 16; ++j)
-                                hv[j] = (j < ncol && row < P.N) ? a.h[(size_t)(c0 + j) * P.N + row] : 0.0f;
-                        }
-                        float vg[16], vu[16];
+                        float hv[16], vg[16], vu[16];
+                        if (full_row) load_resid(a, P, l.nt, c0, ncol, r_in, hv);
                         tmem_ld16(tbase + c0, vg);
                         if (paired) tmem_ld16(tbase + NPAD + c0, vu);
 #pragma unroll
@@ -637,37 +762,52 @@ __global__ void __launch_bounds__(192, 1)
                             if (!has_g) vg[j] = 0.0f;
                             if (!paired || !has_u) vu[j] = 0.0f;
                         }
-                        if (fin) {
-                            if (paired) add_pieces<NPAD, true>(a, vg, vu, u1, re, T, c0, ncol, r_in, tag);
-                            else add_pieces<NPAD, false>(a, vg, vu, u1, re, T, c0, ncol, r_in, tag);
-                        }
-                        float hsq[16];
+                        if (full_row) {
+                            emit_chunk(a, P, l.nt, c0, ncol, r_in, vg, vu, hv, rstd, qd, lane, et, ss_w);
+                        } else {
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) hsq[j] = 0.0f;
-                        if (row < P.N) {
-#pragma unroll
-                            for (int j = 0; j < 16; ++j) {
-                                const int m = c0 + j;
-                                if (j >= ncol) continue;
-                                const size_t o = (size_t)m * P.N + row;
-                                if (P.mode == MODE_SCALED) {
-                                    P.out[o] = __float2bfloat16_rn(vg[j] * rstd[m]);
-                                } else if (P.mode == MODE_RESID) {
-                                    const float hn = hv[j] + vg[j];
-                                    a.h[o] = hn;
-                                    a.hb[o] = __float2bfloat16_rn(hn);
-                                    hsq[j] = hn * hn;
-                                } else {
-                                    P.out[o] = __float2bfloat16_rn(silu(vg[j] * rstd[m]) * (vu[j] * rstd[m]));
-                                }
+                            for (int j = 0; j < 16; j += 4) {
+                                __stcg(reinterpret_cast<float4 *>(mypart + c0 + j),
+                                       make_float4(vg[j], vg[j + 1], vg[j + 2], vg[j + 3]));
+                                if (paired)
+                                    __stcg(reinterpret_cast<float4 *>(mypart + 128 * NPAD + c0 + j),
+                                           make_float4(vu[j], vu[j + 1], vu[j + 2], vu[j + 3]));
                             }
                         }
-                        if (P.mode == MODE_RESID) tile_squares(hsq, c0, qd, lane, et, ss_w, a.ss_rows + (size_t)l.nt * 64);
                     }
                     tc_fence_before();
                     mbar_arrive(&tempty[bf]);
+                    if (!full_row) {
+                        asm volatile("bar.sync 1, 128;" ::: "memory");
+                        const uint32_t c_first = cta_of_unit(rs, G, T), c_last = cta_of_unit(re - 1, G, T);
+                        if (et == 0) {
+                            // CTAs in [c_first, c_last] with an empty range (a stage
+                            // with fewer units than CTAs) hold no piece of the row
+                            uint32_t pieces = 0;
+                            for (uint32_t c = c_first; c <= c_last; ++c)
+                                pieces += ((uint64_t)c * T / G < ((uint64_t)c + 1) * T / G) ? 1u : 0u;
+                            const uint32_t old = atom_add_acq_rel(P.rowcnt + l.nt, 1u);
+                            *last_flag = (old == pieces - 1) ? 1u : 0u;
+                        }
+                        asm volatile("bar.sync 1, 128;" ::: "memory");
+                        if (*last_flag) {
+                            const int ps_first = ((uint64_t)c_first * T / G < rs) ? 1 : 0;
+#pragma unroll 1
+                            for (int c0 = 0; c0 < a.M; c0 += 16) {
+                                const int ncol = min(16, a.M - c0);
+                                float hv[16], ag[16], au[16];
+#pragma unroll
+                                for (int j = 0; j < 16; ++j) ag[j] = au[j] = 0.0f;
+                                if (paired) sum_pieces<NPAD, true>(a, ag, au, c_first, c_last, ps_first, T, r_in, c0);
+                                else sum_pieces<NPAD, false>(a, ag, au, c_first, c_last, ps_first, T, r_in, c0);
+                                load_resid(a, P, l.nt, c0, ncol, r_in, hv);  // 16 loads in flight at once
+                                emit_chunk(a, P, l.nt, c0, ncol, r_in, ag, au, hv, rstd, qd, lane, et, ss_w);
+                            }
+                            if (et == 0) P.rowcnt[l.nt] = 0;  // ready for the next launch
+                        }
+                    }
+                    u = send;
                 }
-                u = send;
             }
             // this CTA's outputs of the stage are written (and, after a residual
             // update, its sums of squares): arrive
@@ -775,10 +915,14 @@ cloak_status stack_decode_run(cloak_ctx *ctx, const cloak_stack_desc *d, float *
     // workspace: bf16 activations, partial sums, counters, barrier
     const size_t act_elems = (size_t)M * (D + HQ + 2 * HKV + F);
     const size_t part_words = (size_t)G * 2 * 128 * PSTRIDE;  // tagged 64-bit words
+    const size_t partf_floats = npad > 16 ? (size_t)G * 2 * 2 * 128 * npad : 0;
+    size_t rows = 0;
+    for (int l = 0; l < d->num_layers; ++l)
+        for (int j = 0; j < 7; ++j) rows += ctx->info[d->layer_tensors[l * 7 + j]].nt;
     const size_t nstages = 4 * (size_t)d->num_layers;
     auto r256 = [](size_t n) { return (n + 255) & ~(size_t)255; };
     const size_t bytes = r256((size_t)M * D * 2) + r256((size_t)M * HQ * 2) + 2 * r256((size_t)M * HKV * 2) +
-                         r256((size_t)M * F * 2) + r256(part_words * 8) + r256(16) +
+                         r256((size_t)M * F * 2) + r256(part_words * 8) + r256(16) + r256(partf_floats * 4) + r256(rows * 4) +
                          r256(nstages * sizeof(StackStage)) + r256((size_t)(D / 128 + 1) * 64 * 4);
     (void)act_elems;
     cudaError_t err = cudaSuccess;
@@ -804,10 +948,13 @@ cloak_status stack_decode_run(cloak_ctx *ctx, const cloak_stack_desc *d, float *
     __nv_bfloat16 *kb = (__nv_bfloat16 *)take((size_t)M * HKV * 2);
     __nv_bfloat16 *vb = (__nv_bfloat16 *)take((size_t)M * HKV * 2);
     __nv_bfloat16 *ab = (__nv_bfloat16 *)take((size_t)M * F * 2);
+    float *partf = (float *)take(partf_floats * 4);
+    uint32_t *cnt = (uint32_t *)take(rows * 4);
     StackStage *dst = (StackStage *)take(nstages * sizeof(StackStage));
     float *ss = (float *)take((size_t)(D / 128 + 1) * 64 * 4);  // [D/128][64] row tiles, then [64] input
     // the stage program
     std::vector<StackStage> st(nstages);
+    size_t roff = 0;
     auto prob = [&](StackProb &P, int t, int t2, int xmap, int xratio, int mode, __nv_bfloat16 *out,
                     uint64_t u_begin) {
         const TensorInfo &ti = ctx->info[t];
@@ -822,6 +969,8 @@ cloak_status stack_decode_run(cloak_ctx *ctx, const cloak_stack_desc *d, float *
         P.xratio = xratio;
         P.mode = mode;
         P.out = out;
+        P.rowcnt = cnt + roff;
+        roff += ti.nt;
         return (uint64_t)ti.nt * P.upr;
     };
     for (int l = 0; l < d->num_layers; ++l) {
@@ -842,6 +991,7 @@ cloak_status stack_decode_run(cloak_ctx *ctx, const cloak_stack_desc *d, float *
         Cs.np = 1;
         Cs.need_rstd = 1;
         Cs.total = prob(Cs.p[0], lt[4], lt[5], XMAP_H, 1, MODE_SWIGLU, ab, 0);
+        roff += ctx->info[lt[5]].nt;  // counters of the paired tensor are unused; keep layout simple
         Dd = StackStage{};
         Dd.np = 1;
         Dd.total = prob(Dd.p[0], lt[6], -1, XMAP_ACT, 1, MODE_RESID, nullptr, 0);
@@ -856,6 +1006,7 @@ cloak_status stack_decode_run(cloak_ctx *ctx, const cloak_stack_desc *d, float *
         CLOAK_CUDA(ctx, cudaStreamSynchronize(s));
         ctx->stack_sig.swap(sig);
     }
+    CLOAK_CUDA(ctx, cudaMemsetAsync(cnt, 0, rows * 4, s));
     CLOAK_CUDA(ctx, cudaMemsetAsync(bar, 0, 8, s));
     k_stack_input<<<M, 256, 0, s>>>(h, D, hb, ss + (size_t)(D / 128) * 64, bar + 2);
     CLOAK_LAUNCHED(ctx);
@@ -878,6 +1029,7 @@ cloak_status stack_decode_run(cloak_ctx *ctx, const cloak_stack_desc *d, float *
     a.h = h;
     a.hb = hb;
     a.part = part;
+    a.partf = partf;
     a.epoch = bar + 2;
     a.ss_rows = ss;
     a.ss_init = ss + (size_t)(D / 128) * 64;
