@@ -190,6 +190,20 @@ CLOAK_API cloak_status cloak_linear_batch(cloak_ctx *ctx, int32_t n, const int32
 CLOAK_API cloak_status cloak_linear_host(cloak_ctx *ctx, int32_t tensor, const void *x_host, void *y_host,
                                int32_t M, int32_t out_dtype, int32_t flags, void *stream);
 
+/* cloak_linear_batch from host buffers: the n inputs are copied in, the
+ * grouped launch runs, the n outputs are copied back and the stream is waited
+ * for (synchronous). Inputs that lie back to back in host memory (x_host[i+1]
+ * == x_host[i] + its size) move in one copy, and so do such outputs, so a
+ * caller that packs a step's vectors pays one copy each way. Pinned host
+ * memory gives asynchronous DMA; pageable memory works but is staged by the
+ * driver. Staging on the device is context-owned (grown with cudaMalloc).
+ * Same rules as cloak_linear_batch otherwise. Paper: the authorised view of
+ * Section 4.2 driven from the host, the way a serving engine hands the layer
+ * one step's activations. */
+CLOAK_API cloak_status cloak_linear_batch_host(cloak_ctx *ctx, int32_t n, const int32_t *tensors,
+                                               const void *const *x_host, void *const *y_host, int32_t M,
+                                               int32_t out_dtype, int32_t flags, void *stream);
+
 /* cloak_linear for callers that cannot allocate device memory while they
  * run: code inside CUDA stream capture (an allocation there breaks the
  * capture), serving loops under a memory pool that owns every byte, or

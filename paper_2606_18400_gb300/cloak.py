@@ -91,6 +91,8 @@ SIGNATURES = [
     ("cloak_linear_batch", _i32, [_vp, _i32, C.POINTER(_i32), C.POINTER(_vp), C.POINTER(_vp), _i32,
                                   _i32, _i32, _vp]),
     ("cloak_linear_host", _i32, [_vp, _i32, _vp, _vp, _i32, _i32, _i32, _vp]),
+    ("cloak_linear_batch_host", _i32, [_vp, _i32, C.POINTER(_i32), C.POINTER(_vp), C.POINTER(_vp), _i32,
+                                       _i32, _i32, _vp]),
     ("cloak_linear_noalloc", _i32, [_vp, _i32, _vp, _vp, _i32, _i32, _i32, _vp]),
     ("cloak_stack_decode", _i32, [_vp, C.POINTER(StackDesc), _vp, _i32, _i32, _vp]),
     ("cloak_serve_step", _i32, [_vp, C.POINTER(ServeDesc), C.POINTER(ServeBatch), _vp]),
@@ -215,6 +217,16 @@ def cloak_linear_host(ctx, tensor: int, x_host: int, y_host: int, M: int, out_dt
                       flags: int = 0, stream=None):
     _check("cloak_linear_host", load().cloak_linear_host(ctx, tensor, x_host, y_host, M, out_dtype,
                                                          flags, _stream(stream)), ctx)
+
+
+def cloak_linear_batch_host(ctx, tensors, x_hosts, y_hosts, M: int, out_dtype: int, flags: int = 0,
+                            stream=None):
+    n = len(tensors)
+    ta = (C.c_int32 * n)(*tensors)
+    xa = (C.c_void_p * n)(*x_hosts)
+    ya = (C.c_void_p * n)(*y_hosts)
+    _check("cloak_linear_batch_host", load().cloak_linear_batch_host(ctx, n, ta, xa, ya, M, out_dtype,
+                                                                     flags, _stream(stream)), ctx)
 
 
 def cloak_linear_noalloc(ctx, tensor: int, x_dev: int, y_dev: int, M: int, out_dtype: int,

@@ -384,6 +384,78 @@ extern "C" cloak_status cloak_linear_host(cloak_ctx *ctx, int32_t tensor, const 
     return CLOAK_OK;
 }
 
+extern "C" cloak_status cloak_linear_batch_host(cloak_ctx *ctx, int32_t n, const int32_t *tensors,
+                                                const void *const *x_host, void *const *y_host, int32_t M,
+                                                int32_t out_dtype, int32_t flags, void *stream) {
+    if (!ctx || n < 1 || n > 8 || !tensors || !x_host || !y_host || M < 1 || M > 65536 ||
+        (out_dtype != CLOAK_OUT_F32 && out_dtype != CLOAK_OUT_BF16) || (flags & ~3))
+        return CLOAK_E_INVAL;
+    for (int i = 0; i < n; ++i)
+        if (tensors[i] < 0 || tensors[i] >= (int32_t)ctx->tensors.size() || !x_host[i] || !y_host[i])
+            return CLOAK_E_INVAL;
+    if (!ctx->keyed) return CLOAK_E_STATE;
+    CLOAK_CUDA(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t xes = ctx->dtype == CLOAK_F32 ? 4 : 2, yes = out_dtype == CLOAK_OUT_F32 ? 4 : 2;
+    // staging: the inputs back to back (each at a 256-byte boundary), then the outputs
+    size_t xoff[8], yoff[8], xb[8], yb[8], tot = 0;
+    for (int i = 0; i < n; ++i) {
+        const cloak_tensor_desc &td = ctx->tensors[tensors[i]];
+        xb[i] = (size_t)M * td.k * xes;
+        xoff[i] = tot;
+        tot += (xb[i] + 255) & ~(size_t)255;
+    }
+    for (int i = 0; i < n; ++i) {
+        const cloak_tensor_desc &td = ctx->tensors[tensors[i]];
+        yb[i] = (size_t)M * td.n * yes;
+        yoff[i] = tot;
+        tot += (yb[i] + 255) & ~(size_t)255;
+    }
+    if (tot > ctx->xstage_cap) {
+        if (ctx->d_xstage) CLOAK_CUDA(ctx, cudaFree(ctx->d_xstage));
+        ctx->d_xstage = nullptr;
+        CLOAK_CUDA(ctx, cudaMalloc(&ctx->d_xstage, tot));
+        ctx->xstage_cap = tot;
+    }
+    uint8_t *stage = (uint8_t *)ctx->d_xstage;
+    // one copy per run of buffers that are contiguous on both sides
+    auto copy_runs = [&](bool in) -> cloak_status {
+        int i = 0;
+        while (i < n) {
+            const uint8_t *h0 = (const uint8_t *)(in ? x_host[i] : y_host[i]);
+            const size_t d0 = in ? xoff[i] : yoff[i];
+            size_t len = in ? xb[i] : yb[i];
+            int j = i + 1;
+            for (; j < n; ++j) {
+                const uint8_t *hj = (const uint8_t *)(in ? x_host[j] : y_host[j]);
+                const size_t dj = in ? xoff[j] : yoff[j];
+                if (hj != h0 + len || dj != d0 + len) break;
+                len += in ? xb[j] : yb[j];
+            }
+            if (in)
+                CLOAK_CUDA(ctx, cudaMemcpyAsync(stage + d0, h0, len, cudaMemcpyHostToDevice, s));
+            else
+                CLOAK_CUDA(ctx, cudaMemcpyAsync((void *)h0, stage + d0, len, cudaMemcpyDeviceToHost, s));
+            i = j;
+        }
+        return CLOAK_OK;
+    };
+    cloak_status rc = copy_runs(true);
+    if (rc) return rc;
+    const void *xd[8];
+    void *yd[8];
+    for (int i = 0; i < n; ++i) {
+        xd[i] = stage + xoff[i];
+        yd[i] = stage + yoff[i];
+    }
+    rc = cloak_linear_batch(ctx, n, tensors, xd, yd, M, out_dtype, flags, stream);
+    if (rc) return rc;
+    rc = copy_runs(false);
+    if (rc) return rc;
+    CLOAK_CUDA(ctx, cudaStreamSynchronize(s));
+    return CLOAK_OK;
+}
+
 extern "C" cloak_status cloak_stack_decode(cloak_ctx *ctx, const cloak_stack_desc *desc, float *h_dev,
                                            int32_t M, int32_t flags, void *stream) {
     if (!ctx || !desc || !desc->layer_tensors || !h_dev || ((uintptr_t)h_dev & 15) || (flags & ~1))

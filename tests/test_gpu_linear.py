@@ -136,6 +136,42 @@ def test_linear_host_entry_point(cloak_lib):
     cm.close()
 
 
+@pytest.mark.parametrize("layout", ["packed", "separate", "pageable"])
+def test_batch_host_entry_point(cloak_lib, layout):
+    """The grouped launch from host buffers equals the same launch on device
+    buffers bit for bit, whether the host vectors lie back to back (one copy
+    each way), apart, or in pageable memory."""
+    m = synth.small_decoder(1, synth.DT_BF16, d_model=384, n_heads=6, n_kv_heads=2, d_ff=200)
+    cm, om, tb, arena, scales, Ws = place_both(cloak_lib, m, key=0x5A)
+    M = 3
+    ts = list(range(len(m.tensors)))
+    xs = [torch.from_numpy(synth.activations_host(M, m.tensors[t].k, seed=70 + t)).to(torch.bfloat16)
+          for t in ts]
+    pin = layout != "pageable"
+    if layout == "packed":
+        xbuf = torch.cat([x.reshape(-1) for x in xs]).pin_memory()
+        ybuf = torch.empty(sum(M * m.tensors[t].n for t in ts), dtype=torch.float32).pin_memory()
+        xh, yh, o, q = [], [], 0, 0
+        for t, x in zip(ts, xs):
+            xh.append(xbuf[o:o + x.numel()].view(M, -1))
+            o += x.numel()
+            yh.append(ybuf[q:q + M * m.tensors[t].n].view(M, -1))
+            q += M * m.tensors[t].n
+    else:
+        xh = [x.pin_memory() if pin else x.clone() for x in xs]
+        yh = [torch.empty((M, m.tensors[t].n), dtype=torch.float32) for t in ts]
+        if pin:
+            yh = [y.pin_memory() for y in yh]
+    cloak_lib.cloak_linear_batch_host(cm.ctx, ts, [x.data_ptr() for x in xh], [y.data_ptr() for y in yh],
+                                      M, cloak_lib.OUT_F32)
+    yd = cm.linear_batch(ts, [x.cuda() for x in xs], out_dtype=cloak_lib.OUT_F32)
+    torch.cuda.synchronize()
+    for y, d in zip(yh, yd):
+        assert torch.equal(y, d.cpu())
+    assert cm.device_status() == 0
+    cm.close()
+
+
 def test_bad_calls_return_errors(cloak_lib):
     m = synth.small_decoder(1, synth.DT_BF16)
     cm = cloak_lib.CloakModel(m)
