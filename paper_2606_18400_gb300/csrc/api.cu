@@ -47,6 +47,23 @@ bool encode_tmap_2d(CUtensorMap *map, CUtensorMapDataType dt, const void *base, 
     return r == CUDA_SUCCESS;
 }
 
+// 3-D tiled map (inner, middle, outer) with strides in bytes for the two
+// outer dimensions; box (box_inner, box_mid, 1); same swizzle as above
+bool encode_tmap_3d(CUtensorMap *map, CUtensorMapDataType dt, const void *base, uint64_t inner,
+                    uint64_t mid, uint64_t outer, uint64_t mid_bytes, uint64_t outer_bytes,
+                    uint32_t box_inner, uint32_t box_mid) {
+    CUtensorMap probe;
+    if (!encode_tmap_2d(&probe, dt, base, inner, mid, mid_bytes, box_inner, box_mid)) return false;
+    cuuint64_t dims[3] = {inner, mid, outer};
+    cuuint64_t strides[2] = {mid_bytes, outer_bytes};
+    cuuint32_t box[3] = {box_inner, box_mid, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = g_encode(map, dt, 3, const_cast<void *>(base), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
 }  // namespace cloak
 
 static int esize_of(int32_t dt) { return dt == CLOAK_F32 ? 4 : dt == CLOAK_BF16 ? 2 : dt == CLOAK_E4M3 ? 1 : 0; }
@@ -145,7 +162,7 @@ static void release(cloak_ctx *c) {
     F(c->d_page_alloc); F(c->d_tile_slot); F(c->d_page_new); F(c->d_tile_inv); F(c->d_info);
     F(c->arena); F(c->twin); F(c->d_scales); F(c->d_part); F(c->d_rowcnt); F(c->d_xq);
     F(c->d_xs); F(c->d_xstage); F(c->d_ystage); F(c->d_plan); F(c->d_status);
-    F(c->d_stack_ws); F(c->d_serve_ws); F(c->rk.d_owner);
+    F(c->d_stack_ws); F(c->d_serve_ws); F(c->rk.d_owner); F(c->d_xqp); F(c->d_xsg);
     if (c->rk.copied) cudaEventDestroy(c->rk.copied);
     if (c->rk.published) cudaEventDestroy(c->rk.published);
     KeygenWork &w = c->kw;

@@ -89,6 +89,10 @@ struct cloak_ctx {
     uint8_t *d_xq = nullptr;                   // quantised activations
     float *d_xs = nullptr;                     // activation scales
     size_t xq_cap = 0;
+    uint8_t *d_xqp = nullptr;                  // per-CTA quantised activations (FP8 decode)
+    size_t xqp_cap = 0;
+    float *d_xsg = nullptr;                    // per-token activation scales (FP8 prefill)
+    size_t xsg_cap = 0;
     void *d_xstage = nullptr, *d_ystage = nullptr;  // host-call staging
     size_t xstage_cap = 0, ystage_cap = 0;
     uint8_t *d_stage = nullptr;                // re-key staging pages (arena pages
@@ -141,6 +145,9 @@ cloak_status cuda_fail(cloak_ctx *ctx, cudaError_t e, const char *where);
 
 bool encode_tmap_2d(CUtensorMap *map, CUtensorMapDataType dt, const void *base, uint64_t inner,
                     uint64_t outer, uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer);
+bool encode_tmap_3d(CUtensorMap *map, CUtensorMapDataType dt, const void *base, uint64_t inner,
+                    uint64_t mid, uint64_t outer, uint64_t mid_bytes, uint64_t outer_bytes,
+                    uint32_t box_inner, uint32_t box_mid);
 
 // keygen.cu
 cloak_status keygen_tables(cloak_ctx *ctx, uint64_t key, uint32_t epoch, cudaStream_t s);
@@ -181,6 +188,10 @@ cloak_status autotune_stack_run(cloak_ctx *ctx, const cloak_stack_desc *d, const
 int stack_l2_prefetch(const cloak_ctx *ctx, const cloak_stack_desc *d, int M);
 cloak_status tune_save(const cloak_ctx *ctx, const char *path);
 cloak_status tune_load(cloak_ctx *ctx, const char *path, int32_t *entries);
+// gemm.cu: prefill-shaped batches (whole 256x256 output tiles per CTA)
+cloak_status gemm_run(cloak_ctx *ctx, int n, const int32_t *tensors, const void *const *xs,
+                      const float *const *x_scales, void *const *ys, int M, int out_f32, int relu,
+                      const uint32_t *slot_of, const CUtensorMap &tw, cudaStream_t s);
 cloak_status linear_run_given_scratch(cloak_ctx *ctx, int t, const void *x, void *y, int M,
                                       int out_dtype, int flags, float *part, size_t part_floats,
                                       uint32_t *rowcnt, uint32_t max_grid, cudaStream_t s);

@@ -138,14 +138,19 @@ __global__ void k_quant_rows_multi(QuantJobs j) {
 // ------------------------------------------------------ tensor-core path
 
 // One launch computes up to MAXP independent linears ("problems"); their
-// tiles are concatenated, (problem, tile row, tile column)-major, and split
-// evenly over the CTAs. A decoder layer's seven linears fit one launch.
+// units are concatenated, (problem, tile row, unit)-major, and split evenly
+// over the CTAs. A decoder layer's seven linears fit one launch. A unit is
+// 32 KiB of weights: one 128x128 BF16 tile, or two consecutive 128x128 E4M3
+// tiles of a row (the last unit of a row with an odd tile count holds one), so
+// both types pay the per-unit costs of the pipeline (ring barriers, MMA
+// commit, loop bookkeeping) once per 32 KiB.
 constexpr int MAXP = 8;
 
 struct TcProblem {
-    uint64_t u_begin;                // first unit (tile) of the problem in the launch
+    uint64_t u_begin;                // first unit of the problem in the launch
     uint32_t base;                   // first logical tile of the tensor
     int N, K, NT, KT;
+    int UPR;                         // units per tile row: KT (BF16) or ceil(KT / 2) (E4M3)
     void *y;
     const float *w_scale, *x_scale;  // E4M3 only
     uint32_t *rowcnt;                // per tile row arrival counters (zeroed)
@@ -155,6 +160,9 @@ struct TcBatch {
     const uint32_t *slot_of;  // gather table; nullptr: uncloaked (slot = tile index)
     int np, M, out_f32, relu;
     int dep_wait;             // launched as a programmatic dependent of the quantiser
+    int fuse_quant;           // E4M3, M <= 4: each CTA quantises its activations itself
+    const __nv_bfloat16 *xsrc[MAXP];  // fused: BF16 activations of each problem
+    uint8_t *xq[MAXP];        // fused: per-CTA codes, [grid][M][K] per problem
     int stages;               // ring depth in use (1 .. TcCfg::STAGES)
     uint64_t total;           // units of all problems
     float *part;              // [grid][2][128][NPAD] partial sums
@@ -168,14 +176,16 @@ struct TxMaps {
 
 template <bool FP8, int NPAD>
 struct TcCfg {
-    static constexpr int A_BYTES = FP8 ? 16384 : 32768;
-    static constexpr int B_BYTES = NPAD * (FP8 ? 128 : 256);
+    // a unit: two 16 KiB halves of A (the two 64-column halves of a BF16 tile,
+    // or two E4M3 tiles) and the two matching 128-byte-wide halves of B
+    static constexpr int A_BYTES = 32768;
+    static constexpr int B_BYTES = NPAD * 256;
     static constexpr int STAGE = A_BYTES + B_BYTES;
     static constexpr int STAGES = std::min(16, (220 * 1024) / STAGE);
-    static constexpr int KSTEPS = FP8 ? 4 : 8;  // MMAs per 128-wide tile
+    static constexpr int KSTEPS = 8;  // MMAs per unit (K = 16 BF16 or K = 32 E4M3 each)
     static constexpr int TMEM_COLS = (2 * NPAD <= 32) ? 32 : (2 * NPAD <= 64) ? 64
                                    : (2 * NPAD <= 128) ? 128 : (2 * NPAD <= 256) ? 256 : 512;
-    static constexpr int SMEM = STAGES * STAGE + 1024 + 512;  // align + barriers
+    static constexpr int SMEM = STAGES * STAGE + 1024 + 1024;  // align + barriers, scales
     static constexpr uint32_t IDESC = idesc_make(FP8 ? 0u : 1u, 128, NPAD);
 };
 
@@ -193,26 +203,37 @@ __device__ __forceinline__ Loc locate(const TcBatch &b, uint64_t u) {
     const uint64_t local = u - b.p[p].u_begin;
     Loc l;
     l.p = p;
-    l.nt = (uint32_t)(local / (uint32_t)b.p[p].KT);
-    l.kt = (uint32_t)(local % (uint32_t)b.p[p].KT);
-    l.row_begin = b.p[p].u_begin + (uint64_t)l.nt * b.p[p].KT;
+    l.nt = (uint32_t)(local / (uint32_t)b.p[p].UPR);
+    l.kt = (uint32_t)(local % (uint32_t)b.p[p].UPR);
+    l.row_begin = b.p[p].u_begin + (uint64_t)l.nt * b.p[p].UPR;
     return l;
 }
 
-// arena slot of unit u (0 past the end): gather-table read, or the tile
-// index itself for the uncloaked twin
-__device__ __forceinline__ uint32_t slot_for(const TcBatch &b, uint64_t u, uint64_t u1) {
+// arena slots of unit u's tiles (0 past the end; s1 = NONE when the unit holds
+// one tile): gather-table reads, or the tile indices themselves for the
+// uncloaked twin
+template <bool FP8>
+__device__ __forceinline__ uint32_t slot_for(const TcBatch &b, uint64_t u, uint64_t u1, uint32_t &s1) {
+    s1 = NONE;
     if (u >= u1) return 0;
     int p = 0;
     while (p + 1 < b.np && u >= b.p[p + 1].u_begin) ++p;
-    const uint32_t g = b.p[p].base + (uint32_t)(u - b.p[p].u_begin);
+    const TcProblem &P = b.p[p];
+    const uint32_t local = (uint32_t)(u - P.u_begin);
+    if (!FP8) {
+        const uint32_t g = P.base + local;
+        return b.slot_of ? __ldg(b.slot_of + g) : g;
+    }
+    const uint32_t nt = local / (uint32_t)P.UPR, j = local - nt * (uint32_t)P.UPR;
+    const uint32_t t0 = 2 * j, g = P.base + nt * (uint32_t)P.KT + t0;
+    if (t0 + 1 < (uint32_t)P.KT) s1 = b.slot_of ? __ldg(b.slot_of + g + 1) : g + 1;
     return b.slot_of ? __ldg(b.slot_of + g) : g;
 }
 
 template <bool FP8>
 __device__ __forceinline__ void store_out(const TcBatch &b, const TcProblem &P, int row, int m,
-                                          float v) {
-    if (FP8) v = v * P.w_scale[row] * P.x_scale[m];
+                                          float v, float w_scale, const float *x_scale) {
+    if (FP8) v = v * w_scale * x_scale[m];
     if (b.relu) v = fmaxf(v, 0.0f);
     if (b.out_f32) reinterpret_cast<float *>(P.y)[(int64_t)m * P.N + row] = v;
     else reinterpret_cast<__nv_bfloat16 *>(P.y)[(int64_t)m * P.N + row] = __float2bfloat16_rn(v);
@@ -231,8 +252,11 @@ __global__ void __launch_bounds__(192, 1)
     uint64_t *empty = full + NS;
     uint64_t *tfull = empty + NS;
     uint64_t *tempty = tfull + 2;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tempty + 2);
+    uint64_t *xready = tempty + 2;  // fused quantisation: this CTA's codes are written
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(xready + 1);
     volatile uint32_t *last_flag = tmem_slot + 1;
+    float *xs_s = reinterpret_cast<float *>(tmem_slot + 4);   // [MAXP][16] fused scales
+    float *red = xs_s + MAXP * 16;                           // [4] warp maxima
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint64_t T = b.total, G = gridDim.x;
@@ -243,6 +267,7 @@ __global__ void __launch_bounds__(192, 1)
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
+        mbar_init(xready, 128);
         for (int i = 0; i < 2; ++i) {
             mbar_init(&tfull[i], 1);
             mbar_init(&tempty[i], 128);
@@ -266,33 +291,46 @@ __global__ void __launch_bounds__(192, 1)
         // critical path); lane 0 waits on the ring and issues the copies.
         const uint64_t pol_w = policy_evict_first(), pol_x = policy_evict_last();
         Loc l = locate(b, u0);
-        uint32_t cur = slot_for(b, u0 + lane, u1), nxt = slot_for(b, u0 + 32 + lane, u1);
+        uint32_t cur1, nxt1;
+        uint32_t cur = slot_for<FP8>(b, u0 + lane, u1, cur1), nxt = slot_for<FP8>(b, u0 + 32 + lane, u1, nxt1);
         uint32_t it = 0;
         // as a dependent launch, weight tiles are requested at once; the
         // activation halves of the first ring slots wait for the quantiser
-        bool waited = !b.dep_wait;
+        bool waited = !b.dep_wait && !b.fuse_quant;
         int pend_n = 0;
-        int pend_s[16], pend_p[16];
+        int pend_s[16], pend_p[16], pend_two[16];
         int32_t pend_kc[16];
-        auto issue_x = [&](int s, int p, int32_t kc) {
+        // the activation halves of a unit: columns kc.. and the next 128 bytes
+        // (64 BF16 / 128 E4M3 values), the second only when the unit has it
+        auto issue_x = [&](int s, int p, int32_t kc, int two) {
             uint8_t *sb = smem + s * C::STAGE + C::A_BYTES;
             const CUtensorMap *xm = &tx.m[p];
+            const int32_t half = FP8 ? 128 : 64;
+            if (FP8 && b.fuse_quant) {
+                // this CTA's own codes: plane blockIdx.x of the problem's 3-D map
+                tma_load_3d_hint(sb, xm, &full[s], kc, 0, (int32_t)blockIdx.x, pol_x);
+                if (two) tma_load_3d_hint(sb + C::B_BYTES / 2, xm, &full[s], kc + half, 0, (int32_t)blockIdx.x, pol_x);
+                return;
+            }
             tma_load_2d_hint(sb, xm, &full[s], kc, 0, pol_x);
-            if (!FP8) tma_load_2d_hint(sb + C::B_BYTES / 2, xm, &full[s], kc + 64, 0, pol_x);
+            if (two) tma_load_2d_hint(sb + C::B_BYTES / 2, xm, &full[s], kc + half, 0, pol_x);
         };
         auto release = [&]() {
-            griddep_wait();
+            if (b.fuse_quant) mbar_wait(xready, 0, b.status);
+            else griddep_wait();
             waited = true;
-            for (int q = 0; q < pend_n; ++q) issue_x(pend_s[q], pend_p[q], pend_kc[q]);
+            for (int q = 0; q < pend_n; ++q) issue_x(pend_s[q], pend_p[q], pend_kc[q], pend_two[q]);
             pend_n = 0;
         };
         for (uint64_t u = u0; u < u1; ++u, ++it) {
             const uint32_t j = (uint32_t)((u - u0) & 31);
             if (j == 0 && u > u0) {
                 cur = nxt;
-                nxt = slot_for(b, u + 32 + lane, u1);
+                cur1 = nxt1;
+                nxt = slot_for<FP8>(b, u + 32 + lane, u1, nxt1);
             }
             const uint32_t slot = __shfl_sync(0xffffffffu, cur, j);
+            const uint32_t slot1 = __shfl_sync(0xffffffffu, cur1, j);
             const int s = it % NS;
             const uint32_t ph = (it / NS) & 1;
             bool ok = true;
@@ -303,23 +341,27 @@ __global__ void __launch_bounds__(192, 1)
             if (!__shfl_sync(0xffffffffu, (int)ok, 0)) break;
             const TcProblem &P = b.p[l.p];
             if (lane == 0) {
-                mbar_expect_tx(&full[s], C::STAGE);
+                // BF16: both 64-column halves of one tile; E4M3: two tiles
+                const int two = (!FP8 || slot1 != NONE) ? 1 : 0;
+                mbar_expect_tx(&full[s], two ? C::STAGE : (C::A_BYTES + C::B_BYTES) / 2);
                 const int32_t row = (int32_t)(slot * 128u);
-                const int32_t kc = (int32_t)l.kt * 128;
+                const int32_t kc = (int32_t)l.kt * (FP8 ? 256 : 128);
                 uint8_t *sa = smem + s * C::STAGE;
                 tma_load_2d_hint(sa, &tw, &full[s], 0, row, pol_w);
                 if (!FP8) tma_load_2d_hint(sa + 16384, &tw, &full[s], 64, row, pol_w);
+                else if (two) tma_load_2d_hint(sa + 16384, &tw, &full[s], 0, (int32_t)(slot1 * 128u), pol_w);
                 if (waited) {
-                    issue_x(s, l.p, kc);
+                    issue_x(s, l.p, kc, two);
                 } else {
                     pend_s[pend_n] = s;
                     pend_p[pend_n] = l.p;
                     pend_kc[pend_n] = kc;
+                    pend_two[pend_n] = two;
                     ++pend_n;
                 }
             }
-            // advance (problem, row, column)
-            if (++l.kt == (uint32_t)P.KT) {
+            // advance (problem, row, unit)
+            if (++l.kt == (uint32_t)P.UPR) {
                 l.kt = 0;
                 if (++l.nt == (uint32_t)P.NT) {
                     l.nt = 0;
@@ -334,7 +376,8 @@ __global__ void __launch_bounds__(192, 1)
             bool ok = true;
             for (uint64_t u = u0; u < u1 && ok; ++seg) {
                 const Loc l = locate(b, u);
-                const uint64_t send = umin64(u1, l.row_begin + b.p[l.p].KT);
+                const TcProblem &P = b.p[l.p];
+                const uint64_t send = umin64(u1, l.row_begin + P.UPR);
                 const uint32_t bf = seg & 1, use = seg >> 1;
                 if (seg >= 2 && !mbar_wait(&tempty[bf], (use - 1) & 1, b.status)) break;
                 tc_fence_after();
@@ -344,16 +387,13 @@ __global__ void __launch_bounds__(192, 1)
                     if (!mbar_wait(&full[s], (it / NS) & 1, b.status)) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t sa = smem_u32(smem + s * C::STAGE), sb = sa + C::A_BYTES;
+                    // an E4M3 row with an odd tile count ends in a one-tile unit
+                    const int nk = (FP8 && (P.KT & 1) && uu - l.row_begin == (uint64_t)P.UPR - 1) ? 4 : 8;
 #pragma unroll
                     for (int kk = 0; kk < C::KSTEPS; ++kk) {
-                        uint32_t ao, bo;
-                        if (FP8) {
-                            ao = kk * 32;
-                            bo = kk * 32;
-                        } else {
-                            ao = (kk >> 2) * 16384 + (kk & 3) * 32;
-                            bo = (kk >> 2) * (C::B_BYTES / 2) + (kk & 3) * 32;
-                        }
+                        if (kk >= nk) break;
+                        const uint32_t ao = (kk >> 2) * 16384 + (kk & 3) * 32;
+                        const uint32_t bo = (kk >> 2) * (C::B_BYTES / 2) + (kk & 3) * 32;
                         const uint64_t ad = sdesc_sw128(sa + ao), bd = sdesc_sw128(sb + bo);
                         if (FP8) umma_f8(d, ad, bd, C::IDESC, (uu > u || kk > 0) ? 1u : 0u);
                         else umma_f16(d, ad, bd, C::IDESC, (uu > u || kk > 0) ? 1u : 0u);
@@ -370,15 +410,90 @@ __global__ void __launch_bounds__(192, 1)
         const int r_in = qd * 32 + lane;
         const int et = threadIdx.x - 64;  // 0..127
         if (b.dep_wait) griddep_wait();  // the activation scales come from the quantiser
+        if (FP8 && b.fuse_quant) {
+            // Decode batches (M <= 4): quantise the activations of the problems
+            // this CTA's range touches into its own slice of the scratch, per
+            // token s = amax/448 (1 for a zero row), codes E4M3(x / s) with
+            // satfinite -- the arithmetic of k_quant_rows_multi -- while the
+            // weight ring fills. The TMA then reads the slice.
+            const int pa = locate(b, u0).p, pz = locate(b, u1 - 1).p;
+            for (int p = pa; p <= pz; ++p) {
+                const int K = b.p[p].K;
+                const __nv_bfloat16 *xsrc = b.xsrc[p];
+                uint8_t *dst = b.xq[p] + (size_t)blockIdx.x * b.M * K;
+                // rows up to XR x 1024 values are read once into registers (one
+                // round of loads in flight); wider rows are read twice in a loop
+                constexpr int XR = 20;
+                const bool fits = K <= XR * 1024;
+                for (int m = 0; m < b.M; ++m) {
+                    const __nv_bfloat16 *xr = xsrc + (size_t)m * K;
+                    uint8_t *qrow = dst + (size_t)m * K;
+                    uint4 w[XR];
+                    float mx = 0.0f;
+                    auto amax8 = [&](const uint4 &v) {
+                        const __nv_bfloat162 *h2 = reinterpret_cast<const __nv_bfloat162 *>(&v);
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const float2 f = __bfloat1622float2(h2[i]);
+                            mx = fmaxf(mx, fmaxf(fabsf(f.x), fabsf(f.y)));
+                        }
+                    };
+                    if (fits) {
+#pragma unroll
+                        for (int i = 0; i < XR; ++i) {
+                            const int k = (i * 128 + et) * 8;
+                            w[i] = k < K ? __ldcg(reinterpret_cast<const uint4 *>(xr + k)) : make_uint4(0u, 0u, 0u, 0u);
+                        }
+#pragma unroll
+                        for (int i = 0; i < XR; ++i) amax8(w[i]);
+                    } else {
+                        for (int k = et * 8; k < K; k += 128 * 8) amax8(__ldcg(reinterpret_cast<const uint4 *>(xr + k)));
+                    }
+                    for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+                    if (lane == 0) red[qd] = mx;
+                    asm volatile("bar.sync 1, 128;" ::: "memory");
+                    mx = fmaxf(fmaxf(red[0], red[1]), fmaxf(red[2], red[3]));
+                    const float sc = mx > 0.0f ? __fdiv_rn(mx, 448.0f) : 1.0f;
+                    if (et == 0) xs_s[p * 16 + m] = sc;
+                    auto quant8 = [&](const uint4 &v, int k) {
+                        const __nv_bfloat162 *h2 = reinterpret_cast<const __nv_bfloat162 *>(&v);
+                        uint32_t q[2] = {0u, 0u};
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const float2 f = __bfloat1622float2(h2[i]);
+                            const uint32_t lo = __nv_cvt_float_to_fp8(__fdiv_rn(f.x, sc), __NV_SATFINITE, __NV_E4M3);
+                            const uint32_t hi = __nv_cvt_float_to_fp8(__fdiv_rn(f.y, sc), __NV_SATFINITE, __NV_E4M3);
+                            q[i >> 1] |= (lo | (hi << 8)) << ((i & 1) * 16);
+                        }
+                        *reinterpret_cast<uint2 *>(qrow + k) = make_uint2(q[0], q[1]);
+                    };
+                    if (fits) {
+#pragma unroll
+                        for (int i = 0; i < XR; ++i) {
+                            const int k = (i * 128 + et) * 8;
+                            if (k < K) quant8(w[i], k);
+                        }
+                    } else {
+                        for (int k = et * 8; k < K; k += 128 * 8) quant8(__ldcg(reinterpret_cast<const uint4 *>(xr + k)), k);
+                    }
+                    asm volatile("bar.sync 1, 128;" ::: "memory");  // red[] is reused per token
+                }
+            }
+            fence_proxy_async_global();  // the codes are read by TMA (async proxy)
+            mbar_arrive(xready);
+        }
         const Loc first = locate(b, u0);
         uint32_t seg = 0;
         for (uint64_t u = u0; u < u1; ++seg) {
             const Loc l = locate(b, u);
             const TcProblem &P = b.p[l.p];
-            const uint64_t rs = l.row_begin, re = rs + P.KT;
+            const float *xsc = (FP8 && b.fuse_quant) ? xs_s + l.p * 16 : P.x_scale;
+            const uint64_t rs = l.row_begin, re = rs + P.UPR;
             const uint64_t send = umin64(u1, re);
             const bool full_row = (u == rs) && (send == re);
             const uint32_t bf = seg & 1, use = seg >> 1;
+            // the row's weight scale, loaded before the accumulator is waited for
+            const float wsc = (FP8 && (int)(l.nt * 128) + r_in < P.N) ? P.w_scale[l.nt * 128 + r_in] : 0.0f;
             if (!mbar_wait(&tfull[bf], use & 1, b.status)) break;
             tc_fence_after();
             const int row = (int)(l.nt * 128) + r_in;
@@ -393,7 +508,7 @@ __global__ void __launch_bounds__(192, 1)
                     if (row < P.N) {
 #pragma unroll
                         for (int j = 0; j < 16; ++j)
-                            if (c0 + j < b.M) store_out<FP8>(b, P, row, c0 + j, v[j]);
+                            if (c0 + j < b.M) store_out<FP8>(b, P, row, c0 + j, v[j], wsc, xsc);
                     }
                 } else {
 #pragma unroll
@@ -449,7 +564,7 @@ __global__ void __launch_bounds__(192, 1)
                         if (row < P.N) {
 #pragma unroll
                             for (int j = 0; j < 16; ++j)
-                                if (c0 + j < b.M) store_out<FP8>(b, P, row, c0 + j, acc[j]);
+                                if (c0 + j < b.M) store_out<FP8>(b, P, row, c0 + j, acc[j], wsc, xsc);
                         }
                     }
                     if (et == 0) P.rowcnt[l.nt] = 0;  // ready for the next launch
@@ -478,18 +593,43 @@ static cloak_status launch_tc(cloak_ctx *ctx, const CUtensorMap &tw, const void 
     }
     TxMaps tx;
     const int es = FP8 ? 1 : 2;
-    for (int p = 0; p < b.np; ++p) {
-        if (!encode_tmap_2d(&tx.m[p], FP8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
-                            xs[p], (uint64_t)b.p[p].K, (uint64_t)b.M, (uint64_t)b.p[p].K * es,
-                            128 / es, NPAD)) {
-            ctx->last_err = "cuTensorMapEncodeTiled failed for x";
-            return CLOAK_E_CUDA;
-        }
-    }
     b.stages = (cfg.stages >= 1 && cfg.stages <= C::STAGES) ? cfg.stages : C::STAGES;
     const uint32_t want = cfg.grid > 0 ? (uint32_t)cfg.grid : (uint32_t)ctx->sm_count;
     const uint32_t grid = (uint32_t)std::min<uint64_t>(b.total, want);
-    const size_t smem = (size_t)b.stages * C::STAGE + 1024 + 512;
+    if (FP8 && b.fuse_quant) {
+        // each CTA's own codes: per problem, [grid][M][K] bytes, read through a
+        // 3-D map whose outer coordinate is the CTA
+        size_t kall = 0;
+        for (int p = 0; p < b.np; ++p) kall += (size_t)b.p[p].K;
+        const size_t need = (size_t)grid * b.M * kall;
+        if (need > ctx->xqp_cap) {
+            if (ctx->d_xqp) CLOAK_CUDA(ctx, cudaFree(ctx->d_xqp));
+            ctx->d_xqp = nullptr;
+            CLOAK_CUDA(ctx, cudaMalloc(&ctx->d_xqp, need));
+            ctx->xqp_cap = need;
+        }
+        size_t off = 0;
+        for (int p = 0; p < b.np; ++p) {
+            const uint64_t K = (uint64_t)b.p[p].K;
+            b.xq[p] = ctx->d_xqp + off;
+            off += (size_t)grid * b.M * K;
+            if (!encode_tmap_3d(&tx.m[p], CU_TENSOR_MAP_DATA_TYPE_UINT8, b.xq[p], K, (uint64_t)b.M, grid, K,
+                                K * (uint64_t)b.M, 128, NPAD)) {
+                ctx->last_err = "cuTensorMapEncodeTiled failed for the per-CTA codes";
+                return CLOAK_E_CUDA;
+            }
+        }
+    } else {
+        for (int p = 0; p < b.np; ++p) {
+            if (!encode_tmap_2d(&tx.m[p], FP8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                                xs[p], (uint64_t)b.p[p].K, (uint64_t)b.M, (uint64_t)b.p[p].K * es,
+                                128 / es, NPAD)) {
+                ctx->last_err = "cuTensorMapEncodeTiled failed for x";
+                return CLOAK_E_CUDA;
+            }
+        }
+    }
+    const size_t smem = (size_t)b.stages * C::STAGE + 1024 + 1024;
     const size_t need = (size_t)grid * 2 * 128 * NPAD;
     if (need > ctx->part_cap) {
         if (ctx->d_part) CLOAK_CUDA(ctx, cudaFree(ctx->d_part));
@@ -537,7 +677,7 @@ int tc_max_stages(bool fp8, int npad) {
     }
 }
 
-int tc_stage_bytes(bool fp8, int npad) { return (fp8 ? 16384 : 32768) + npad * (fp8 ? 128 : 256); }
+int tc_stage_bytes(bool fp8, int npad) { return 32768 + npad * 256; }
 
 int tc_npad(int m) { return m <= 16 ? 16 : m <= 32 ? 32 : m <= 64 ? 64 : m <= 128 ? 128 : 256; }
 
@@ -566,7 +706,52 @@ cloak_status linear_batch_run(cloak_ctx *ctx, int n, const int32_t *tensors, con
     TuneCfg cfg = tune_lookup(ctx, n, tensors, M, out_dtype);
     if (ctx->tune_invariant) cfg.grid = 0;  // the split over CTAs fixes the summation order
     const int chunk = cfg.chunk > 0 ? cfg.chunk : 256;
-    if (fp8) {
+    // prefill-shaped batches: whole 256x256 output tiles per CTA (gemm.cu),
+    // unless the tuner chose narrower token chunks for this shape
+    if (M >= 256 && (cfg.chunk == 0 || cfg.chunk >= 256)) {
+        const void *xg[MAXP];
+        const float *sg[MAXP] = {};
+        if (fp8) {
+            // all M rows quantised in one launch: codes [M, K] and scales [M] per problem
+            size_t qb = 0;
+            for (int p = 0; p < n; ++p) qb += (size_t)M * ctx->info[tensors[p]].k;
+            if (qb > ctx->xq_cap) {
+                if (ctx->d_xq) CLOAK_CUDA(ctx, cudaFree(ctx->d_xq));
+                ctx->d_xq = nullptr;
+                CLOAK_CUDA(ctx, cudaMalloc(&ctx->d_xq, qb));
+                ctx->xq_cap = qb;
+            }
+            if ((size_t)n * M > ctx->xsg_cap) {
+                if (ctx->d_xsg) CLOAK_CUDA(ctx, cudaFree(ctx->d_xsg));
+                ctx->d_xsg = nullptr;
+                CLOAK_CUDA(ctx, cudaMalloc(&ctx->d_xsg, (size_t)n * M * sizeof(float)));
+                ctx->xsg_cap = (size_t)n * M;
+            }
+            QuantJobs qj{};
+            size_t qoff = 0;
+            for (int p = 0; p < n; ++p) {
+                const int k = ctx->info[tensors[p]].k;
+                qj.x[p] = (const __nv_bfloat16 *)xs[p];
+                qj.q[p] = ctx->d_xq + qoff;
+                qj.s[p] = ctx->d_xsg + (size_t)p * M;
+                qj.K[p] = k;
+                xg[p] = qj.q[p];
+                sg[p] = qj.s[p];
+                qoff += (size_t)M * k;
+            }
+            k_quant_rows_multi<<<dim3(M, n), 256, 0, s>>>(qj);
+            CLOAK_LAUNCHED(ctx);
+        } else {
+            for (int p = 0; p < n; ++p) xg[p] = xs[p];
+        }
+        const CUtensorMap &twg = unc ? ctx->tmap_twin : ctx->tmap_arena;
+        return gemm_run(ctx, n, tensors, xg, sg, ys, M, out_dtype == CLOAK_OUT_F32, relu, slot_of, twg, s);
+    }
+    // E4M3 decode batches quantise their activations inside the linear (each
+    // CTA for the problems it touches); this needs K a multiple of 16
+    bool fuse = fp8 && M <= 4;
+    for (int p = 0; p < n && fuse; ++p) fuse = ctx->info[tensors[p]].k % 16 == 0;
+    if (fp8 && !fuse) {
         size_t qb = 0;
         for (int p = 0; p < n; ++p) qb += (size_t)std::min(M, chunk) * ctx->info[tensors[p]].k;
         if (qb > ctx->xq_cap) {
@@ -600,11 +785,17 @@ cloak_status linear_batch_run(cloak_ctx *ctx, int n, const int32_t *tensors, con
             P.K = ti.k;
             P.NT = ti.nt;
             P.KT = ti.kt;
+            P.UPR = fp8 ? (ti.kt + 1) / 2 : ti.kt;
             P.y = (uint8_t *)ys[p] + (size_t)m0 * ti.n * oes;
             P.rowcnt = ctx->d_rowcnt + ti.row_off;
-            u += (uint64_t)ti.nt * ti.kt;
+            u += (uint64_t)ti.nt * P.UPR;
             const uint8_t *x = (const uint8_t *)xs[p] + (size_t)m0 * ti.k * 2;  // BF16 activations
-            if (fp8) {
+            if (fuse) {
+                b.xsrc[p] = (const __nv_bfloat16 *)x;
+                P.w_scale = ctx->d_scales + ti.scale_off;
+                P.x_scale = nullptr;
+                xm[p] = nullptr;
+            } else if (fp8) {
                 uint8_t *q = ctx->d_xq + qoff;
                 float *sc = ctx->d_xs + p * 256;
                 qoff += (size_t)mb * ti.k;
@@ -620,7 +811,8 @@ cloak_status linear_batch_run(cloak_ctx *ctx, int n, const int32_t *tensors, con
             }
         }
         b.total = u;
-        if (fp8) {
+        b.fuse_quant = fuse ? 1 : 0;
+        if (fp8 && !fuse) {
             k_quant_rows_multi<<<dim3(mb, n), 256, 0, s>>>(qj);
             CLOAK_LAUNCHED(ctx);
             b.dep_wait = 1;
@@ -679,6 +871,7 @@ cloak_status linear_run_given_scratch(cloak_ctx *ctx, int t, const void *x, void
     P.K = ti.k;
     P.NT = ti.nt;
     P.KT = ti.kt;
+    P.UPR = ti.kt;
     P.y = y;
     P.rowcnt = rowcnt;
     b.total = (uint64_t)ti.nt * ti.kt;

@@ -110,6 +110,15 @@ CLOAK_DEV void tma_load_2d_hint(void *dst, const CUtensorMap *m, uint64_t *bar, 
         "l"(reinterpret_cast<uint64_t>(m)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "l"(policy)
         : "memory");
 }
+// 3-D tiled load (x, y, z coordinates) with an L2 cache hint
+CLOAK_DEV void tma_load_3d_hint(void *dst, const CUtensorMap *m, uint64_t *bar, int32_t c0, int32_t c1,
+                                int32_t c2, uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1, {%3, %4, %5}], [%2], %6;" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(m)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "l"(policy)
+        : "memory");
+}
 CLOAK_DEV uint64_t policy_evict_first() {
     uint64_t p;
     asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
@@ -143,6 +152,9 @@ CLOAK_DEV void bulk_wait_read() {
 template <int N>
 CLOAK_DEV void bulk_wait() {
     asm volatile("cp.async.bulk.wait_group %0;" ::"n"(N) : "memory");
+}
+CLOAK_DEV void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 CLOAK_DEV void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");

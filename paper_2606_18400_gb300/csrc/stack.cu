@@ -173,9 +173,6 @@ __device__ __forceinline__ bool bar_wait(const StackArgs &a, uint64_t *bar, uint
     }
 }
 
-__device__ __forceinline__ void fence_proxy_async_global() {
-    asm volatile("fence.proxy.async.global;" ::: "memory");
-}
 
 // The epilogue's first thread is the CTA's only poller of the grid barrier; it
 // publishes the stage whose inputs are complete to the producer in shared

@@ -69,10 +69,13 @@ static std::vector<TuneCfg> candidates(const cloak_ctx *ctx, int n, const int32_
         depths.erase(std::unique(depths.begin(), depths.end()), depths.end());
         for (int st : depths) {
             if (st < 2 || st > maxs) continue;
-            const int smem = st * sb + 1536;
+            const int smem = st * sb + 2048;
             const int per_sm = std::min((228 * 1024) / (smem + 1024), 512 / tmem_cols(np));
             std::vector<int> grids = {sm, sm / 2};
-            if (per_sm >= 2) grids.push_back(2 * sm);
+            // several CTAs per SM: independent producers and MMA issuers hide the
+            // per-tile issue latency of small (E4M3) tiles
+            for (int k = 2; k <= 4; ++k)
+                if (per_sm >= k) grids.push_back(k * sm);
             if (rows < sm * std::max(per_sm, 1)) grids.push_back(rows);
             std::sort(grids.begin(), grids.end());
             grids.erase(std::unique(grids.begin(), grids.end()), grids.end());

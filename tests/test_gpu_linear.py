@@ -51,7 +51,7 @@ def test_small_bf16_decoder_all_tensors(cloak_lib, M):
     cm.close()
 
 
-@pytest.mark.parametrize("M", [1, 4, 16, 64, 200])
+@pytest.mark.parametrize("M", [1, 4, 16, 64, 200, 300])
 def test_small_fp8_decoder_all_tensors(cloak_lib, M):
     m = synth.small_decoder(2, synth.DT_E4M3, page_bytes=2 * 128 * 128, d_model=384, n_heads=6,
                             n_kv_heads=2, d_ff=256)
@@ -61,15 +61,41 @@ def test_small_fp8_decoder_all_tensors(cloak_lib, M):
     cm.close()
 
 
-def test_fp8_quantised_operands_are_near_exact(cloak_lib):
+@pytest.mark.parametrize("M", [1, 3, 16, 260])
+def test_fp8_quantised_operands_are_near_exact(cloak_lib, M):
     """With the oracle's quantised activations the only difference left is
-    FP32 accumulation order: far below the 5e-2 bound."""
+    FP32 accumulation order: far below the 5e-2 bound (M <= 4 quantises inside
+    the linear, M = 16 in the separate quantiser)."""
     m = synth.small_decoder(1, synth.DT_E4M3, page_bytes=2 * 128 * 128, d_model=512, d_ff=512,
                             n_heads=4, n_kv_heads=4, head_dim=128)
     cm, om, tb, arena, scales, Ws = place_both(cloak_lib, m, key=9)
     for t in range(len(m.tensors)):
-        err = check_tensor(cloak_lib, cm, om, tb, arena, scales, t, 16, seed=t)
+        err = check_tensor(cloak_lib, cm, om, tb, arena, scales, t, M, seed=t)
         assert err < 1e-5
+    cm.close()
+
+
+@pytest.mark.parametrize("grouped", [False, True])
+def test_fp8_fused_quantisation_equals_separate(cloak_lib, grouped):
+    """Decode batches (M <= 4) quantise their activations inside the linear;
+    wider batches run the separate quantiser. A row's result depends only on
+    its own token's codes and scale, and M = 4 and M = 5 share the tile shape
+    and the split over CTAs, so the first four rows must agree bit for bit."""
+    m = synth.small_decoder(2, synth.DT_E4M3, page_bytes=2 * 128 * 128, d_model=384, n_heads=6,
+                            n_kv_heads=2, d_ff=256)
+    cm, om, tb, arena, scales, Ws = place_both(cloak_lib, m, key=0x3C)
+    ts = [i for i, t in enumerate(m.tensors) if t.layer == 1]
+    xs = [x_device(m, synth.activations_host(5, m.tensors[t].k, seed=90 + t)) for t in ts]
+    if grouped:
+        y5 = cm.linear_batch(ts, xs, out_dtype=cloak_lib.OUT_F32)
+        y4 = cm.linear_batch(ts, [x[:4].contiguous() for x in xs], out_dtype=cloak_lib.OUT_F32)
+    else:
+        y5 = [cm.linear(t, x, out_dtype=cloak_lib.OUT_F32) for t, x in zip(ts, xs)]
+        y4 = [cm.linear(t, x[:4].contiguous(), out_dtype=cloak_lib.OUT_F32) for t, x in zip(ts, xs)]
+    torch.cuda.synchronize()
+    for a, b in zip(y4, y5):
+        assert torch.equal(a, b[:4])
+    assert cm.device_status() == 0
     cm.close()
 
 
@@ -188,7 +214,7 @@ def test_bad_calls_return_errors(cloak_lib):
     cm.close()
 
 
-@pytest.mark.parametrize("M", [1, 8, 64])
+@pytest.mark.parametrize("M", [1, 8, 64, 300])
 def test_batched_layer_launch(cloak_lib, M):
     """All seven linears of a decoder layer in one launch (one split over
     their concatenated tiles): each output within tolerance of the oracle,
@@ -236,4 +262,29 @@ def test_batched_full_layer(cloak_lib):
     for t, x, y, u in zip(ts, xs_h, ys, yu):
         assert O.relative_error(y.cpu().numpy(), O.cloaked_linear(om, tb, t, arena, x)) <= 1e-2
         assert torch.equal(y, u)
+    cm.close()
+
+
+@pytest.mark.parametrize("M", [512])
+def test_full_layer_prefill_sampled(cloak_lib, M):
+    """Prefill of the full 7B-class layer in one grouped launch (whole 256x256
+    output tiles per CTA): a keyed sample of 48 output features of every
+    tensor, all tokens, against the FP64 product on the stored weights; the
+    cloaked and uncloaked launches agree bit for bit on the whole output."""
+    m = synth.llama7b_layer(1)
+    cm, om, tb, arena, scales, Ws = place_both(cloak_lib, m, key=0x1234)
+    ts = list(range(7))
+    xs_h = [synth.activations_host(M, m.tensors[t].k, seed=300 + t) for t in ts]
+    xs = [x_device(m, x) for x in xs_h]
+    ys = cm.linear_batch(ts, xs, out_dtype=cloak_lib.OUT_F32)
+    yu = cm.linear_batch(ts, xs, out_dtype=cloak_lib.OUT_F32, uncloaked=True)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(0x5EED)
+    for t, x, y, u in zip(ts, xs_h, ys, yu):
+        assert torch.equal(y, u)
+        rows = np.sort(rng.choice(m.tensors[t].n, 48, replace=False))
+        W64 = O.stored_f64(om, tb, t, arena)[rows]
+        ref = O.linear_f64(O.x_operand(om, x), W64)
+        err = O.relative_error(y.cpu().numpy()[:, rows], ref)
+        assert err <= 1e-2, (t, err)
     cm.close()
