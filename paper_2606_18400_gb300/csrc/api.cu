@@ -162,7 +162,7 @@ static void release(cloak_ctx *c) {
     F(c->d_page_alloc); F(c->d_tile_slot); F(c->d_page_new); F(c->d_tile_inv); F(c->d_info);
     F(c->arena); F(c->twin); F(c->d_scales); F(c->d_part); F(c->d_rowcnt); F(c->d_xq);
     F(c->d_xs); F(c->d_xstage); F(c->d_ystage); F(c->d_plan); F(c->d_status);
-    F(c->d_stack_ws); F(c->d_serve_ws); F(c->rk.d_owner); F(c->d_xqp); F(c->d_xsg);
+    F(c->d_stack_ws); F(c->d_serve_ws); F(c->rk.d_owner); F(c->d_xqp); F(c->d_xsg); F(c->d_gemm_next);
     if (c->rk.copied) cudaEventDestroy(c->rk.copied);
     if (c->rk.published) cudaEventDestroy(c->rk.published);
     KeygenWork &w = c->kw;

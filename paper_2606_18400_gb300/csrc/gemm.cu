@@ -11,6 +11,9 @@
 // row-pair-major, token-chunk-minor, so the CTAs working at one time share a
 // few row pairs: each weight tile is fetched from HBM once and then hit in L2
 // by the other token chunks, and the activations (a few MB) stay in L2.
+// Problems are ordered longest rows first and tiles are handed out by an
+// atomic counter (each CTA's first tile is its own index), so the last tiles
+// to start are short ones and no CTA is left with two long ones.
 //
 // A K "slab" is 128 bytes wide: half of a 128x128 BF16 tile (64 columns) or a
 // whole 128x128 E4M3 tile. The same code serves both types; E4M3 applies the
@@ -43,6 +46,7 @@ struct GemmArgs {
     const uint32_t *slot_of;  // gather table; nullptr: uncloaked (slot = tile index)
     int np, M, out_f32, relu;
     uint32_t items;
+    uint32_t *next;           // tiles handed out after each CTA's first (zeroed per launch)
     int *status;
     GemmProblem p[GMAXP];
 };
@@ -58,6 +62,7 @@ struct GemmCfg {
     static constexpr int STAGE = 2 * A_HALF + B_BYTES;
     static constexpr int STAGES = 3;
     static constexpr int SMEM = STAGES * STAGE + 1024 + 1024;
+    static constexpr int QD = 4;                  // depth of the tile-index queue
     static constexpr uint32_t IDESC = idesc_make(FP8 ? 0u : 1u, 128, 256);
 };
 
@@ -99,7 +104,10 @@ __global__ void __launch_bounds__(192, 1)
     uint64_t *empty = full + C::STAGES;
     uint64_t *tfull = empty + C::STAGES;
     uint64_t *tempty = tfull + 1;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tempty + 1);
+    uint64_t *id_full = tempty + 1;     // [QD] a tile index is published
+    uint64_t *id_empty = id_full + C::QD;  // [QD] the MMA thread and all epilogue threads read it
+    uint32_t *ids = reinterpret_cast<uint32_t *>(id_empty + C::QD);
+    uint32_t *tmem_slot = ids + C::QD;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -109,6 +117,10 @@ __global__ void __launch_bounds__(192, 1)
         }
         mbar_init(tfull, 1);
         mbar_init(tempty, 128);
+        for (int q = 0; q < C::QD; ++q) {
+            mbar_init(&id_full[q], 1);
+            mbar_init(&id_empty[q], 129);
+        }
         fence_mbar_init();
         prefetch_tmap(&tw);
         for (int p = 0; p < g.np; ++p) prefetch_tmap(&xm.x[p]);
@@ -127,7 +139,19 @@ __global__ void __launch_bounds__(192, 1)
         const uint64_t pol_w = policy_evict_last(), pol_x = policy_evict_last();
         uint32_t it = 0;  // slab counter over all items (ring position)
         bool ok = true;
-        for (uint32_t item = blockIdx.x; item < g.items && ok; item += gridDim.x) {
+        for (uint32_t n = 0; ok; ++n) {
+            // next tile: publish its index to the MMA and epilogue warps
+            uint32_t item = 0;
+            if (lane == 0) {
+                const int q = n % C::QD;
+                if (n >= (uint32_t)C::QD) ok = mbar_wait(&id_empty[q], ((n / C::QD) & 1) ^ 1, g.status);
+                item = n == 0 ? blockIdx.x : gridDim.x + atomicAdd(g.next, 1u);
+                if (item >= g.items || !ok) item = NONE;
+                ids[q] = item;
+                mbar_arrive(&id_full[q]);
+            }
+            item = __shfl_sync(0xffffffffu, item, 0);
+            if (item == NONE) break;
             const GItem w = gitem(g, item);
             const GemmProblem &P = g.p[w.p];
             const int r0 = 2 * w.rp, r1 = r0 + 1;
@@ -167,7 +191,12 @@ __global__ void __launch_bounds__(192, 1)
         if (lane == 0) {
             uint32_t it = 0, n = 0;
             bool ok = true;
-            for (uint32_t item = blockIdx.x; item < g.items && ok; item += gridDim.x, ++n) {
+            for (;; ++n) {
+                const int q = n % C::QD;
+                if (!mbar_wait(&id_full[q], (n / C::QD) & 1, g.status)) break;
+                const uint32_t item = ids[q];
+                mbar_arrive(&id_empty[q]);
+                if (item == NONE) break;
                 const GItem w = gitem(g, item);
                 const GemmProblem &P = g.p[w.p];
                 // the epilogue has drained the previous tile's accumulators
@@ -194,13 +223,18 @@ __global__ void __launch_bounds__(192, 1)
                 if (!ok) break;
                 umma_commit(tfull);
             }
+            (void)ok;
         }
     } else {
         // ---------------------------------------------------------- epilogue
         const int qd = warp & 3;
         const int r_in = qd * 32 + lane;
-        uint32_t n = 0;
-        for (uint32_t item = blockIdx.x; item < g.items; item += gridDim.x, ++n) {
+        for (uint32_t n = 0;; ++n) {
+            const int q = n % C::QD;
+            if (!mbar_wait(&id_full[q], (n / C::QD) & 1, g.status)) break;
+            const uint32_t item = ids[q];
+            mbar_arrive(&id_empty[q]);
+            if (item == NONE) break;
             const GItem w = gitem(g, item);
             const GemmProblem &P = g.p[w.p];
             float wsc[2] = {1.0f, 1.0f};
@@ -213,24 +247,27 @@ __global__ void __launch_bounds__(192, 1)
             }
             if (!mbar_wait(tfull, n & 1, g.status)) break;
             tc_fence_after();
+            const uint32_t taddr = tmem + ((uint32_t)(qd * 32) << 16);
 #pragma unroll 1
-            for (int h = 0; h < 2; ++h) {
-                if (h == 1 && !w.two) break;
-                const int row = w.rp * 256 + h * 128 + r_in;
-                const uint32_t taddr = tmem + ((uint32_t)(qd * 32) << 16) + h * 256;
-#pragma unroll 1
-                for (int c0 = 0; c0 < 256; c0 += 16) {
-                    const int m0 = w.tc * 256 + c0;
-                    if (m0 >= g.M) break;
+            for (int c0 = 0; c0 < 256; c0 += 16) {
+                const int m0 = w.tc * 256 + c0;
+                if (m0 >= g.M) break;
+                float xsc[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) xsc[j] = (FP8 && m0 + j < g.M) ? P.x_scale[m0 + j] : 1.0f;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    if (h == 1 && !w.two) break;
+                    const int row = w.rp * 256 + h * 128 + r_in;
                     float v[16];
-                    tmem_ld16(taddr + c0, v);
+                    tmem_ld16(taddr + h * 256 + c0, v);
                     if (row >= P.N) continue;
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
                         const int m = m0 + j;
                         if (m >= g.M) break;
                         float o = v[j];
-                        if (FP8) o = o * wsc[h] * P.x_scale[m];
+                        if (FP8) o = o * wsc[h] * xsc[j];
                         if (g.relu) o = fmaxf(o, 0.0f);
                         if (g.out_f32) reinterpret_cast<float *>(P.y)[(int64_t)m * P.N + row] = o;
                         else reinterpret_cast<__nv_bfloat16 *>(P.y)[(int64_t)m * P.N + row] = __float2bfloat16_rn(o);
@@ -309,6 +346,9 @@ cloak_status gemm_run(cloak_ctx *ctx, int n, const int32_t *tensors, const void 
         }
     }
     g.items = items;
+    if (!ctx->d_gemm_next) CLOAK_CUDA(ctx, cudaMalloc(&ctx->d_gemm_next, 256));
+    CLOAK_CUDA(ctx, cudaMemsetAsync(ctx->d_gemm_next, 0, sizeof(uint32_t), s));
+    g.next = (uint32_t *)ctx->d_gemm_next;
     const int grid = (int)std::min<uint32_t>(items, (uint32_t)ctx->sm_count);
     return fp8 ? gemm_launch<true>(ctx, tw, mp, g, grid, s) : gemm_launch<false>(ctx, tw, mp, g, grid, s);
 }

@@ -93,6 +93,7 @@ struct cloak_ctx {
     size_t xqp_cap = 0;
     float *d_xsg = nullptr;                    // per-token activation scales (FP8 prefill)
     size_t xsg_cap = 0;
+    void *d_gemm_next = nullptr;               // prefill tile counter
     void *d_xstage = nullptr, *d_ystage = nullptr;  // host-call staging
     size_t xstage_cap = 0, ystage_cap = 0;
     uint8_t *d_stage = nullptr;                // re-key staging pages (arena pages
