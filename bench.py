@@ -653,7 +653,7 @@ def run_profile(args):
     """Small cases of one kernel each, for ncu captures (a few GB at most):
     stack  -- a 4-layer 7B-class stack (1.6 GB), decode M=1, 3 launches;
     fp8    -- one GQA E4M3 layer (233 MB), grouped decode M=1, 3 launches;
-    prefill-- one 7B-class layer, grouped M=512, 3 launches;
+    prefill-- one 7B-class layer, grouped M=2048 (the prefill GEMM), 3 launches;
     decode -- one 7B-class layer, grouped M=1 (the headline step), 3 launches.
     The linears' launch shape is tuned first (unless --no-tune); the profiled
     launches sit inside the NVTX range "profiled" (ncu --nvtx
@@ -681,7 +681,7 @@ def run_profile(args):
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
     else:
-        M = 512 if args.profile == "prefill" else 1
+        M = 2048 if args.profile == "prefill" else 1
         xs = [torch.from_numpy(synth.activations_host(M, t.k, seed=i)).cuda().to(torch.bfloat16)
               for i, t in enumerate(model.tensors)]
         group = list(range(len(model.tensors)))
