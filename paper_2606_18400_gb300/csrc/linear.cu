@@ -707,8 +707,11 @@ cloak_status linear_batch_run(cloak_ctx *ctx, int n, const int32_t *tensors, con
     if (ctx->tune_invariant) cfg.grid = 0;  // the split over CTAs fixes the summation order
     const int chunk = cfg.chunk > 0 ? cfg.chunk : 256;
     // prefill-shaped batches: whole 256x256 output tiles per CTA (gemm.cu),
-    // unless the tuner chose narrower token chunks for this shape
-    if (M >= 256 && (cfg.chunk == 0 || cfg.chunk >= 256)) {
+    // unless the tuner chose narrower token chunks for this shape, or the
+    // caller needs one summation order for every batch size (serving: a
+    // request's numbers must not depend on what it is batched with; the
+    // stream-K split below depends on the weights only, not on M)
+    if (M >= 256 && !ctx->tune_invariant && (cfg.chunk == 0 || cfg.chunk >= 256)) {
         const void *xg[MAXP];
         const float *sg[MAXP] = {};
         if (fp8) {

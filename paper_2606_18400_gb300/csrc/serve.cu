@@ -214,113 +214,210 @@ __global__ void __launch_bounds__(128) k_attn_combine(const int32_t *pos, const 
 }
 
 // Query-tiled causal attention for runs of consecutive tokens of one request
-// (prefill chunks): a block takes up to 64 queries of one head; each 64-key
-// tile of K and V is staged once in shared memory (FP32) and used by all of
-// them. Thread t: query t/2, dimension half t%2 (64 dims); a score is the
-// sum of the two halves. Online softmax in FP32 over key chunks of 16.
-// tiles: [n][3] = (first batch token, query count, -) ; query i of a tile is
-// batch token first + i, positions consecutive.
+// (prefill chunks), on the tensor cores: a block takes up to 64 queries of
+// one head, 16 per warp. Per 64-key tile (starting at absolute multiples of
+// 64, so a query's result does not depend on the batch it is in): K and V
+// land in shared memory through cp.async (two buffers, the next tile in
+// flight while this one is used; 16-byte chunks XOR-swizzled by row), S =
+// Q K^T with warp-level BF16 MMAs (m16n8k16, FP32 accumulate), causal mask,
+// online softmax in FP32 (exp2 with the 1/sqrt(128) scale folded in), then
+// O += P V with P taken from the S registers as BF16 and V fragments read
+// transposed from shared memory. tiles: [n][3] = (first batch token, query
+// count, -); query i of a tile is batch token first + i, positions
+// consecutive.
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&v);
+}
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(addr));
+}
+__device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(addr));
+}
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, bool valid) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// byte offset of 16-byte chunk c of row r in a [64][256-byte] tile
+__device__ __forceinline__ uint32_t att_sw(int r, int c) { return (uint32_t)(r * 256 + ((c ^ (r & 7)) << 4)); }
+
+constexpr int ATT_TILE_BYTES = 64 * 256;  // 64 keys x 128 BF16 dims
+
 __global__ void __launch_bounds__(128) k_attention_tiled(const __nv_bfloat16 *q, const __nv_bfloat16 *kc,
                                                          const __nv_bfloat16 *vc, const int32_t *pos,
                                                          const int32_t *req, const int32_t *btab,
                                                          const int32_t *tiles, int max_blocks, int HQ,
                                                          int HKV, __nv_bfloat16 *out) {
-    extern __shared__ float sm[];
-    float *Ks = sm, *Vs = sm + 64 * 128;
+    extern __shared__ __align__(128) uint8_t att_smem[];  // [2 buffers][K tile, V tile]
     const int tile = blockIdx.x, j = blockIdx.y, t = threadIdx.x;
+    const int warp = t >> 5, lane = t & 31;
     const int first = tiles[3 * tile], nq = tiles[3 * tile + 1];
-    const int qi = t >> 1, half = t & 1;
     const int kvh = j / (HQ / HKV);
-    const int m = first + min(qi, nq - 1);
     const int r = req[first];
-    const int p = pos[m];
+    const int p0 = pos[first];
     const int p_last = pos[first + nq - 1];
     const int32_t *bt = btab + (size_t)r * max_blocks;
-    float qv[64];
-    const __nv_bfloat16 *qr = q + ((size_t)m * HQ + j) * 128 + half * 64;
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(att_smem);
+    // this thread's two query rows (fragment rows lane/4 and lane/4 + 8)
+    const int qa = warp * 16 + (lane >> 2), qb = qa + 8;
+    const int pa = p0 + qa, pb = p0 + qb;  // positions (beyond the tile: masked, not written)
+    // Q fragments for the 8 k16 steps over the 128 dims
+    uint32_t qf[8][4];
+    {
+        const __nv_bfloat16 *ra = q + ((size_t)(first + min(qa, nq - 1)) * HQ + j) * 128;
+        const __nv_bfloat16 *rb = q + ((size_t)(first + min(qb, nq - 1)) * HQ + j) * 128;
+        const int c = 2 * (lane & 3);
 #pragma unroll
-    for (int d = 0; d < 64; ++d) qv[d] = __bfloat162float(qr[d]) * 0.08838834764831845f;
-    float acc[64];
-#pragma unroll
-    for (int d = 0; d < 64; ++d) acc[d] = 0.0f;
-    float mx = -FLT_MAX, sum = 0.0f;
-    for (int k0 = 0; k0 <= p_last; k0 += 64) {
-        __syncthreads();
-        // stage 64 keys: 128 threads, each 64 of the 8192 values of K and of V
-        for (int e = t; e < 64 * 16; e += 128) {
-            const int kk = e >> 4, part = e & 15;  // 16 parts of 8 dims
-            const int key = k0 + kk;
-            float4 a0 = make_float4(0, 0, 0, 0), a1 = a0, b0 = a0, b1 = a0;
-            if (key <= p_last) {
-                const size_t off = (((size_t)bt[key / 16] * 16 + key % 16) * HKV + kvh) * 128 + part * 8;
-                const uint4 rk = *reinterpret_cast<const uint4 *>(kc + off);
-                const uint4 rv = *reinterpret_cast<const uint4 *>(vc + off);
-                const __nv_bfloat162 *hk = reinterpret_cast<const __nv_bfloat162 *>(&rk);
-                const __nv_bfloat162 *hv = reinterpret_cast<const __nv_bfloat162 *>(&rv);
-                float2 f;
-                f = __bfloat1622float2(hk[0]); a0.x = f.x; a0.y = f.y;
-                f = __bfloat1622float2(hk[1]); a0.z = f.x; a0.w = f.y;
-                f = __bfloat1622float2(hk[2]); a1.x = f.x; a1.y = f.y;
-                f = __bfloat1622float2(hk[3]); a1.z = f.x; a1.w = f.y;
-                f = __bfloat1622float2(hv[0]); b0.x = f.x; b0.y = f.y;
-                f = __bfloat1622float2(hv[1]); b0.z = f.x; b0.w = f.y;
-                f = __bfloat1622float2(hv[2]); b1.x = f.x; b1.y = f.y;
-                f = __bfloat1622float2(hv[3]); b1.z = f.x; b1.w = f.y;
-            }
-            float4 *kd = reinterpret_cast<float4 *>(Ks + kk * 128 + part * 8);
-            float4 *vd = reinterpret_cast<float4 *>(Vs + kk * 128 + part * 8);
-            kd[0] = a0; kd[1] = a1;
-            vd[0] = b0; vd[1] = b1;
-        }
-        __syncthreads();
-        const int kn = min(64, p_last + 1 - k0);
-        for (int c = 0; c < kn; c += 16) {
-            float sc[16];
-#pragma unroll
-            for (int z = 0; z < 16; ++z) {
-                const float *kr = Ks + (c + z) * 128 + half * 64;
-                float d0 = 0.0f;
-#pragma unroll
-                for (int d = 0; d < 64; d += 4) {
-                    const float4 kv = *reinterpret_cast<const float4 *>(kr + d);
-                    d0 = fmaf(qv[d], kv.x, d0);
-                    d0 = fmaf(qv[d + 1], kv.y, d0);
-                    d0 = fmaf(qv[d + 2], kv.z, d0);
-                    d0 = fmaf(qv[d + 3], kv.w, d0);
-                }
-                d0 += __shfl_xor_sync(0xffffffffu, d0, 1);
-                const int key = k0 + c + z;
-                sc[z] = (c + z < kn && key <= p) ? d0 : -FLT_MAX;
-            }
-            float cm = mx;
-#pragma unroll
-            for (int z = 0; z < 16; ++z) cm = fmaxf(cm, sc[z]);
-            const float scale = expf(mx - cm);
-            sum *= scale;
-#pragma unroll
-            for (int d = 0; d < 64; ++d) acc[d] *= scale;
-#pragma unroll
-            for (int z = 0; z < 16; ++z) {
-                const float pz = sc[z] == -FLT_MAX ? 0.0f : expf(sc[z] - cm);
-                sum += pz;
-                const float *vr = Vs + (c + z) * 128 + half * 64;
-#pragma unroll
-                for (int d = 0; d < 64; d += 4) {
-                    const float4 vv = *reinterpret_cast<const float4 *>(vr + d);
-                    acc[d] = fmaf(pz, vv.x, acc[d]);
-                    acc[d + 1] = fmaf(pz, vv.y, acc[d + 1]);
-                    acc[d + 2] = fmaf(pz, vv.z, acc[d + 2]);
-                    acc[d + 3] = fmaf(pz, vv.w, acc[d + 3]);
-                }
-            }
-            mx = cm;
+        for (int s = 0; s < 8; ++s) {
+            qf[s][0] = *reinterpret_cast<const uint32_t *>(ra + 16 * s + c);
+            qf[s][1] = *reinterpret_cast<const uint32_t *>(rb + 16 * s + c);
+            qf[s][2] = *reinterpret_cast<const uint32_t *>(ra + 16 * s + 8 + c);
+            qf[s][3] = *reinterpret_cast<const uint32_t *>(rb + 16 * s + 8 + c);
         }
     }
-    if (qi < nq) {
-        __nv_bfloat16 *o = out + ((size_t)m * HQ + j) * 128 + half * 64;
-        const float inv = 1.0f / sum;
+    float o[16][4];
 #pragma unroll
-        for (int d = 0; d < 64; ++d) o[d] = __float2bfloat16_rn(acc[d] * inv);
+    for (int n = 0; n < 16; ++n) o[n][0] = o[n][1] = o[n][2] = o[n][3] = 0.0f;
+    float ma = -FLT_MAX, mb = -FLT_MAX, la = 0.0f, lb = 0.0f;
+    const float sl2 = 0.08838834764831845f * 1.4426950408889634f;  // 1/sqrt(128) * log2(e)
+
+    // stage key tile kt (64 keys from kt*64) into buffer b: 128 threads x
+    // 8 chunks of K and 8 of V; keys past the last query's position are zero
+    auto stage = [&](int kt, int b) {
+        const uint32_t kd = sbase + b * 2 * ATT_TILE_BYTES, vd = kd + ATT_TILE_BYTES;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int e = i * 128 + t;          // 1024 chunks of 16 bytes per tile
+            const int row = e >> 4, c = e & 15;
+            const int key = kt * 64 + row;
+            const bool ok = key <= p_last;
+            const size_t off = ok ? (((size_t)bt[key / 16] * 16 + key % 16) * HKV + kvh) * 128 + c * 8 : 0;
+            cp_async16(kd + att_sw(row, c), kc + off, ok);
+            cp_async16(vd + att_sw(row, c), vc + off, ok);
+        }
+        cp_async_commit();
+    };
+    const int ntile = p_last / 64 + 1;
+    stage(0, 0);
+    for (int kt = 0; kt < ntile; ++kt) {
+        const int b = kt & 1;
+        if (kt + 1 < ntile) {
+            stage(kt + 1, b ^ 1);  // the other buffer was released at the end of the last tile
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        const uint32_t kd = sbase + b * 2 * ATT_TILE_BYTES, vd = kd + ATT_TILE_BYTES;
+        // S = Q K^T for this warp's 16 queries x 64 keys (8 blocks of 8 keys)
+        float sc[8][4];
+#pragma unroll
+        for (int n = 0; n < 8; ++n) sc[n][0] = sc[n][1] = sc[n][2] = sc[n][3] = 0.0f;
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+#pragma unroll
+            for (int n = 0; n < 8; n += 2) {
+                // matrices: keys n*8.. (dims 16s, 16s+8), keys (n+1)*8.. (same)
+                const int mi = lane >> 3, rr = lane & 7;
+                const int key = (n + (mi >> 1)) * 8 + rr;
+                const int chunk = 2 * s + (mi & 1);
+                uint32_t b0, b1, b2, b3;
+                ldsm_x4(kd + att_sw(key, chunk), b0, b1, b2, b3);
+                mma_bf16(sc[n], qf[s], b0, b1);
+                mma_bf16(sc[n + 1], qf[s], b2, b3);
+            }
+        }
+        // causal mask, online softmax (rows a and b of this thread)
+        float ca = ma, cb = mb;
+#pragma unroll
+        for (int n = 0; n < 8; ++n) {
+            const int k0 = kt * 64 + n * 8 + 2 * (lane & 3);
+            sc[n][0] = (k0 <= pa) ? sc[n][0] * sl2 : -FLT_MAX;
+            sc[n][1] = (k0 + 1 <= pa) ? sc[n][1] * sl2 : -FLT_MAX;
+            sc[n][2] = (k0 <= pb) ? sc[n][2] * sl2 : -FLT_MAX;
+            sc[n][3] = (k0 + 1 <= pb) ? sc[n][3] * sl2 : -FLT_MAX;
+            ca = fmaxf(ca, fmaxf(sc[n][0], sc[n][1]));
+            cb = fmaxf(cb, fmaxf(sc[n][2], sc[n][3]));
+        }
+        ca = fmaxf(ca, __shfl_xor_sync(0xffffffffu, ca, 1));
+        ca = fmaxf(ca, __shfl_xor_sync(0xffffffffu, ca, 2));
+        cb = fmaxf(cb, __shfl_xor_sync(0xffffffffu, cb, 1));
+        cb = fmaxf(cb, __shfl_xor_sync(0xffffffffu, cb, 2));
+        const float fa = (ma == -FLT_MAX) ? 0.0f : exp2f(ma - ca);
+        const float fb = (mb == -FLT_MAX) ? 0.0f : exp2f(mb - cb);
+        ma = ca;
+        mb = cb;
+        float sa = 0.0f, sb = 0.0f;
+        uint32_t pf[4][4];  // P as A fragments for the 4 k16 steps over the 64 keys
+#pragma unroll
+        for (int n = 0; n < 8; ++n) {
+            const float e0 = sc[n][0] == -FLT_MAX ? 0.0f : exp2f(sc[n][0] - ca);
+            const float e1 = sc[n][1] == -FLT_MAX ? 0.0f : exp2f(sc[n][1] - ca);
+            const float e2 = sc[n][2] == -FLT_MAX ? 0.0f : exp2f(sc[n][2] - cb);
+            const float e3 = sc[n][3] == -FLT_MAX ? 0.0f : exp2f(sc[n][3] - cb);
+            sa += e0 + e1;
+            sb += e2 + e3;
+            pf[n >> 1][(n & 1) * 2 + 0] = pack_bf16(e0, e1);
+            pf[n >> 1][(n & 1) * 2 + 1] = pack_bf16(e2, e3);
+        }
+        la = la * fa + sa;
+        lb = lb * fb + sb;
+#pragma unroll
+        for (int n = 0; n < 16; ++n) {
+            o[n][0] *= fa;
+            o[n][1] *= fa;
+            o[n][2] *= fb;
+            o[n][3] *= fb;
+        }
+        // O += P V: 4 k16 steps (keys) x 16 blocks of 8 dims
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+#pragma unroll
+            for (int n = 0; n < 16; n += 2) {
+                // transposed matrices: keys 16s.. / 16s+8.. x dims n*8.., (n+1)*8..
+                const int mi = lane >> 3, rr = lane & 7;
+                const int key = 16 * s + (mi & 1) * 8 + rr;
+                const int chunk = n + (mi >> 1);
+                uint32_t b0, b1, b2, b3;
+                ldsm_x4_t(vd + att_sw(key, chunk), b0, b1, b2, b3);
+                mma_bf16(o[n], pf[s], b0, b1);
+                mma_bf16(o[n + 1], pf[s], b2, b3);
+            }
+        }
+        __syncthreads();  // buffer b is free for the tile after next
+    }
+    // quad sums of the denominators, then the outputs of valid queries
+    la += __shfl_xor_sync(0xffffffffu, la, 1);
+    la += __shfl_xor_sync(0xffffffffu, la, 2);
+    lb += __shfl_xor_sync(0xffffffffu, lb, 1);
+    lb += __shfl_xor_sync(0xffffffffu, lb, 2);
+    const float ia = 1.0f / la, ib = 1.0f / lb;
+    const int c = 2 * (lane & 3);
+    if (qa < nq) {
+        __nv_bfloat16 *oa = out + ((size_t)(first + qa) * HQ + j) * 128;
+#pragma unroll
+        for (int n = 0; n < 16; ++n)
+            *reinterpret_cast<__nv_bfloat162 *>(oa + n * 8 + c) = __floats2bfloat162_rn(o[n][0] * ia, o[n][1] * ia);
+    }
+    if (qb < nq) {
+        __nv_bfloat16 *ob = out + ((size_t)(first + qb) * HQ + j) * 128;
+#pragma unroll
+        for (int n = 0; n < 16; ++n)
+            *reinterpret_cast<__nv_bfloat162 *>(ob + n * 8 + c) = __floats2bfloat162_rn(o[n][2] * ib, o[n][3] * ib);
     }
 }
 
@@ -428,7 +525,7 @@ static cloak_status serve_step_body(cloak_ctx *ctx, const cloak_serve_desc *d,
         static bool attr = false;
         if (!attr) {
             CLOAK_CUDA(ctx, cudaFuncSetAttribute(k_attention_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 2 * 64 * 128 * (int)sizeof(float)));
+                                                 4 * ATT_TILE_BYTES));
             attr = true;
         }
     }
@@ -451,7 +548,7 @@ static cloak_status serve_step_body(cloak_ctx *ctx, const cloak_serve_desc *d,
         CLOAK_LAUNCHED(ctx);
         if (b->qtiles && b->num_qtiles > 0) {
             // prefill runs: query tiles sharing staged K/V tiles
-            k_attention_tiled<<<dim3(b->num_qtiles, HQ), 128, 2 * 64 * 128 * sizeof(float), s>>>(
+            k_attention_tiled<<<dim3(b->num_qtiles, HQ), 128, 4 * ATT_TILE_BYTES, s>>>(
                 q, kc, vc, b->positions, b->req_slots, b->block_tables, b->qtiles, d->max_blocks, HQ,
                 HKV, attn);
             CLOAK_LAUNCHED(ctx);

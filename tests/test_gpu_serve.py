@@ -102,6 +102,20 @@ def test_request_alone_equals_request_in_a_mix(served, tiled):
         assert np.array_equal(x, y)
 
 
+def test_request_alone_equals_request_in_a_wide_mix(served):
+    """A mix of over 256 tokens (the size where standalone linears switch to
+    the prefill GEMM) still gives the request the numbers it gets alone."""
+    m, Ws, sm = served
+    rng = np.random.default_rng(3)
+    a = list(rng.integers(0, 1000, 61))
+    b = list(rng.integers(0, 1000, 230))
+    alone, sa = run_steps(sm, [(0, a)], tiled=True)
+    mixed, sm_ = run_steps(sm, [(1, b), (0, a)], tiled=True)
+    for x, y in zip(alone[0], mixed[0]):
+        assert np.array_equal(x, y)
+    assert sa[0] == sm_[0]
+
+
 def test_server_serves_a_workload_with_rekeys(cloak_lib):
     m = small_served()
     Ws = synth.weights_host(m, seed=0, std=0.05)
