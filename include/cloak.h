@@ -271,8 +271,17 @@ typedef struct {
  * earlier positions must be in the cache or in this batch). sample_rows lists
  * the tokens whose next token is sampled (greedy) into out_tokens;
  * out_logits (FP32 [num_sample, vocab], may be NULL) receives their logits. */
+/* cloak_serve_batch.flags, besides CLOAK_LINEAR_UNCLOAKED: the first
+ * num_single tokens are the batch's decode tokens and the others prompt
+ * tokens. The linears then run the decode rows through the split-K decode
+ * kernel and the prompt rows through the whole-tile prefill kernel; either
+ * kernel's summation order depends on the weights only, so a token's result
+ * still depends only on its own request (and on being a decode or a prompt
+ * token). Without the flag every row takes the decode kernel. */
+enum { CLOAK_SERVE_DECODE_FIRST = 4 };
+
 typedef struct {
-    int32_t num_tokens, num_sample, flags;  /* flags: CLOAK_LINEAR_UNCLOAKED   */
+    int32_t num_tokens, num_sample, flags;  /* CLOAK_LINEAR_UNCLOAKED, CLOAK_SERVE_DECODE_FIRST */
     const int32_t *token_ids, *positions, *req_slots, *block_tables, *sample_rows;
     int32_t *out_tokens;
     float *out_logits;

@@ -21,6 +21,7 @@ F32, BF16, E4M3 = 0, 1, 2
 MODEL_TWIN = 1
 TAB_LAYER_PERM, TAB_GROUP_PERM, TAB_TENSOR_BASE, TAB_TILE_PERM, TAB_PAGE_ALLOC, TAB_TILE_SLOT = range(6)
 LINEAR_UNCLOAKED, LINEAR_RELU = 1, 2
+SERVE_DECODE_FIRST = 4
 OUT_F32, OUT_BF16 = 0, 1
 
 _STATUS = {0: "CLOAK_OK", -1: "CLOAK_E_INVAL", -2: "CLOAK_E_NOMEM", -3: "CLOAK_E_CUDA",

@@ -486,7 +486,9 @@ extern "C" cloak_status cloak_serve_step(cloak_ctx *ctx, const cloak_serve_desc 
                                          const cloak_serve_batch *batch, void *stream) {
     if (!ctx || !desc || !batch || !desc->stack.layer_tensors || !desc->embedding || !desc->k_cache ||
         !desc->v_cache || desc->num_blocks <= 0 || desc->max_blocks <= 0 || desc->vocab <= 0 ||
-        (batch->num_sample > 0 && (!batch->sample_rows || !batch->out_tokens)) || (batch->flags & ~1))
+        (batch->num_sample > 0 && (!batch->sample_rows || !batch->out_tokens)) ||
+        (batch->flags & ~(CLOAK_LINEAR_UNCLOAKED | CLOAK_SERVE_DECODE_FIRST)) ||
+        ((batch->flags & CLOAK_SERVE_DECODE_FIRST) && (batch->num_single < 0 || batch->num_single > batch->num_tokens)))
         return CLOAK_E_INVAL;
     if (!ctx->keyed) return CLOAK_E_STATE;
     if ((batch->flags & CLOAK_LINEAR_UNCLOAKED) && !ctx->twin) return CLOAK_E_STATE;

@@ -24,6 +24,30 @@ namespace cloak {
 
 static inline unsigned nb(size_t n, unsigned b = 256) { return (unsigned)((n + b - 1) / b); }
 
+// The step's linears over rows [0, M): decode rows [0, m_dec) through the
+// split-K decode kernel, prompt rows [m_dec, M) through the whole-tile
+// prefill GEMM. Each kernel's summation order depends on the weights only, so
+// a row's result does not depend on the rest of the batch.
+static cloak_status step_linears(cloak_ctx *ctx, int n, const int32_t *ts, const void *const *xs,
+                                 void *const *ys, int M, int m_dec, int out_dtype, int flags, cudaStream_t s) {
+    cloak_status rc = CLOAK_OK;
+    if (m_dec > 0 && (rc = linear_batch_run(ctx, n, ts, xs, ys, m_dec, out_dtype, flags, s))) return rc;
+    if (M > m_dec) {
+        const int oes = out_dtype == CLOAK_OUT_F32 ? 4 : 2;
+        const void *xp[8];
+        void *yp[8];
+        for (int i = 0; i < n; ++i) {
+            const TensorInfo &ti = ctx->info[ts[i]];
+            xp[i] = (const uint8_t *)xs[i] + (size_t)m_dec * ti.k * 2;
+            yp[i] = (uint8_t *)ys[i] + (size_t)m_dec * ti.n * oes;
+        }
+        const bool unc = flags & CLOAK_LINEAR_UNCLOAKED;
+        rc = gemm_run(ctx, n, ts, xp, nullptr, yp, M - m_dec, out_dtype == CLOAK_OUT_F32, 0,
+                      unc ? nullptr : ctx->d_tile_slot, unc ? ctx->tmap_twin : ctx->tmap_arena, s);
+    }
+    return rc;
+}
+
 __global__ void k_embed(const __nv_bfloat16 *emb, const int32_t *ids, int D, float *h) {
     const int m = blockIdx.x;
     const __nv_bfloat16 *e = emb + (size_t)ids[m] * D;
@@ -485,6 +509,7 @@ static cloak_status serve_step_body(cloak_ctx *ctx, const cloak_serve_desc *d,
         ctx->tensors[d->lm_head].k != D)
         return CLOAK_E_INVAL;
     const int flags = (b->flags & CLOAK_LINEAR_UNCLOAKED);
+    const int m_dec = (b->flags & CLOAK_SERVE_DECODE_FIRST) ? b->num_single : b->num_tokens;
     // workspace: h, y (fp32 [M, max(D, F)]), g, u (fp32 [M, F]), x, attn, q, k, v, act (bf16), logits
     const size_t Mz = (size_t)M;
     auto r256 = [](size_t n) { return (n + 255) & ~(size_t)255; };
@@ -541,7 +566,7 @@ static cloak_status serve_step_body(cloak_ctx *ctx, const cloak_serve_desc *d,
             const int32_t ts[3] = {lt[0], lt[1], lt[2]};
             const void *xs3[3] = {x, x, x};
             void *ys3[3] = {q, k, v};
-            if ((rc = linear_batch_run(ctx, 3, ts, xs3, ys3, M, CLOAK_OUT_BF16, flags, s))) return rc;
+            if ((rc = step_linears(ctx, 3, ts, xs3, ys3, M, m_dec, CLOAK_OUT_BF16, flags, s))) return rc;
         }
         k_rope_cache<<<dim3(M, HQ + HKV), 64, 0, s>>>(q, k, v, b->positions, b->req_slots, b->block_tables,
                                                       d->max_blocks, HQ, HKV, d->rope_theta, kc, vc);
@@ -563,7 +588,12 @@ static cloak_status serve_step_body(cloak_ctx *ctx, const cloak_serve_desc *d,
                                                               attn);
             CLOAK_LAUNCHED(ctx);
         }
-        if ((rc = linear_run(ctx, lt[3], attn, y, M, CLOAK_OUT_F32, flags, s))) return rc;
+        {
+            const int32_t t1[1] = {lt[3]};
+            const void *x1[1] = {attn};
+            void *y1[1] = {y};
+            if ((rc = step_linears(ctx, 1, t1, x1, y1, M, m_dec, CLOAK_OUT_F32, flags, s))) return rc;
+        }
         k_add<<<nb(Mz * D), 256, 0, s>>>(h, y, Mz * D);
         CLOAK_LAUNCHED(ctx);
         k_rmsnorm<<<M, 256, 0, s>>>(h, nullptr, D, sd.rms_eps, x);
@@ -572,11 +602,16 @@ static cloak_status serve_step_body(cloak_ctx *ctx, const cloak_serve_desc *d,
             const int32_t ts[2] = {lt[4], lt[5]};
             const void *xs2[2] = {x, x};
             void *ys2[2] = {g, u};
-            if ((rc = linear_batch_run(ctx, 2, ts, xs2, ys2, M, CLOAK_OUT_F32, flags, s))) return rc;
+            if ((rc = step_linears(ctx, 2, ts, xs2, ys2, M, m_dec, CLOAK_OUT_F32, flags, s))) return rc;
         }
         k_silu_mul<<<nb(Mz * F), 256, 0, s>>>(g, u, act, Mz * F);
         CLOAK_LAUNCHED(ctx);
-        if ((rc = linear_run(ctx, lt[6], act, y, M, CLOAK_OUT_F32, flags, s))) return rc;
+        {
+            const int32_t t1[1] = {lt[6]};
+            const void *x1[1] = {act};
+            void *y1[1] = {y};
+            if ((rc = step_linears(ctx, 1, t1, x1, y1, M, m_dec, CLOAK_OUT_F32, flags, s))) return rc;
+        }
         k_add<<<nb(Mz * D), 256, 0, s>>>(h, y, Mz * D);
         CLOAK_LAUNCHED(ctx);
     }

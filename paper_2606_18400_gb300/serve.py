@@ -80,14 +80,18 @@ class ServedModel:
                                     self.v_cache.data_ptr(), kv_blocks, max_blocks, rope_theta)
 
     def step(self, token_ids, positions, req_slots, block_tables, sample_rows, out_tokens,
-             out_logits=None, uncloaked=False, stream=None, qtiles=None, single_rows=None):
+             out_logits=None, uncloaked=False, stream=None, qtiles=None, single_rows=None,
+             decode_first=False):
         """Run one forward step; all arguments are device int32 tensors
         (out_logits: optional FP32 [num_sample, vocab]; qtiles [n, 3] and
-        single_rows: optional attention work split, see cloak_serve_batch)."""
+        single_rows: optional attention work split, see cloak_serve_batch).
+        decode_first: the single rows are the batch's first rows and its decode
+        tokens (prompt rows then take the prefill GEMM)."""
         nq = int(qtiles.shape[0]) if qtiles is not None else 0
         ns = int(single_rows.numel()) if single_rows is not None else 0
+        flags = (cloak.LINEAR_UNCLOAKED if uncloaked else 0) | (cloak.SERVE_DECODE_FIRST if decode_first else 0)
         b = cloak.ServeBatch(int(token_ids.numel()), int(sample_rows.numel()),
-                             cloak.LINEAR_UNCLOAKED if uncloaked else 0, token_ids.data_ptr(),
+                             flags, token_ids.data_ptr(),
                              positions.data_ptr(), req_slots.data_ptr(), block_tables.data_ptr(),
                              sample_rows.data_ptr(), out_tokens.data_ptr(),
                              out_logits.data_ptr() if out_logits is not None else None, nq, ns,
@@ -217,7 +221,8 @@ class Server:
             self.sm.step(self.d_ids[:M], self.d_pos[:M], self.d_req[:M], self.block_tables,
                          self.d_samp[:S], self.d_out[:S], uncloaked=self.uncloaked,
                          stream=self.stream.cuda_stream,
-                         qtiles=self.d_tiles[:3 * nt].view(-1, 3), single_rows=self.d_single[:ns])
+                         qtiles=self.d_tiles[:3 * nt].view(-1, 3), single_rows=self.d_single[:ns],
+                         decode_first=True)
             self.h_out[:S].copy_(self.d_out[:S], non_blocking=True)
         if between is not None:
             between()

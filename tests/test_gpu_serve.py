@@ -27,7 +27,7 @@ def served(cloak_lib):
     sm.close()
 
 
-def run_steps(sm, seqs, uncloaked=False, tiled=False):
+def run_steps(sm, seqs, uncloaked=False, tiled=False, decode_first=False):
     """Prefill each (slot, tokens) fully in one step, then decode 3 steps
     feeding back greedy tokens; returns per slot the list of logits. With
     `tiled`, prefill tokens use query tiles (64) and decode tokens single rows."""
@@ -58,7 +58,7 @@ def run_steps(sm, seqs, uncloaked=False, tiled=False):
         if tiled:
             qt = T(tiles).view(-1, 3) if tiles else T([]).view(0, 3)
             sm.step(T(ids), T(pos), T(req), bt, T(samp), out, lg, uncloaked=uncloaked, qtiles=qt,
-                    single_rows=T(single))
+                    single_rows=T(single), decode_first=decode_first)
         else:
             sm.step(T(ids), T(pos), T(req), bt, T(samp), out, lg, uncloaked=uncloaked)
         torch.cuda.synchronize()
@@ -68,11 +68,13 @@ def run_steps(sm, seqs, uncloaked=False, tiled=False):
     return logits, state
 
 
-@pytest.mark.parametrize("tiled", [False, True])
-def test_serve_step_matches_full_model_oracle(served, tiled):
+@pytest.mark.parametrize("tiled,decode_first", [(False, False), (True, False), (True, True)])
+def test_serve_step_matches_full_model_oracle(served, tiled, decode_first):
+    """decode_first: the prompt rows take the prefill GEMM, decode rows the
+    split-K kernel."""
     m, Ws, sm = served
     toks = list(np.random.default_rng(1).integers(0, 1000, 23))
-    logits, state = run_steps(sm, [(0, toks)], tiled=tiled)
+    logits, state = run_steps(sm, [(0, toks)], tiled=tiled, decode_first=decode_first)
     W64 = [O.bf16_value(O.bf16_bits(w)) for w in Ws]
     emb64 = O.bf16_value(O.bf16_bits(synth.embedding_host(1000, 512)))
     seq = state[0]
@@ -114,6 +116,57 @@ def test_request_alone_equals_request_in_a_wide_mix(served):
     for x, y in zip(alone[0], mixed[0]):
         assert np.array_equal(x, y)
     assert sa[0] == sm_[0]
+
+
+def test_decode_rows_and_prompt_rows_in_one_step(served):
+    """With decode tokens first (prompt rows through the prefill GEMM, decode
+    rows through the split-K kernel), a request's numbers do not depend on
+    the other requests of the step: request 0 decoding while request 1's
+    prompt is in the same step gets the logits it gets alone, and so does
+    request 1."""
+    m, Ws, sm = served
+    dev = "cuda"
+    rng = np.random.default_rng(4)
+    a = list(rng.integers(0, 1000, 37))
+    b = list(rng.integers(0, 1000, 290))
+    bt = torch.zeros((8, sm.max_blocks), dtype=torch.int32, device=dev)
+    for slot in range(3):
+        bt[slot] = torch.arange(slot * sm.max_blocks, (slot + 1) * sm.max_blocks, dtype=torch.int32)
+    T = lambda v: torch.tensor(v, dtype=torch.int32, device=dev)
+
+    def step(decodes, prompts):
+        """decodes: [(slot, token, position)]; prompts: [(slot, tokens)] whole
+        prompts from position 0. Returns the logits of every sampled row."""
+        ids, pos, req, samp, tiles, single = [], [], [], [], [], []
+        for slot, tok, p in decodes:
+            single.append(len(ids))
+            ids.append(tok); pos.append(p); req.append(slot); samp.append(len(ids) - 1)
+        for slot, toks in prompts:
+            for t0 in range(0, len(toks), 64):
+                tiles += [len(ids) + t0, min(64, len(toks) - t0), 0]
+            for i, t in enumerate(toks):
+                ids.append(t); pos.append(i); req.append(slot)
+            samp.append(len(ids) - 1)
+        out = torch.zeros(len(samp), dtype=torch.int32, device=dev)
+        lg = torch.zeros((len(samp), sm.model.vocab), dtype=torch.float32, device=dev)
+        qt = T(tiles).view(-1, 3) if tiles else T([]).view(0, 3)
+        sm.step(T(ids), T(pos), T(req), bt, T(samp), out, lg, qtiles=qt, single_rows=T(single),
+                decode_first=True)
+        torch.cuda.synchronize()
+        return lg.cpu().numpy(), out.cpu().numpy()
+
+    # alone: request 0 (slot 0) prefills, then decodes one token; request 1
+    # (slot 1) prefills
+    la0, oa0 = step([], [(0, a)])
+    la1, _ = step([(0, int(oa0[0]), len(a))], [])
+    lb, _ = step([], [(2, b)])
+    # mixed: request 0 prefills (slot 1), then its decode token shares a
+    # step with request 1's prompt (slot 2 again)
+    lm0, om0 = step([], [(1, a)])
+    lm1, _ = step([(1, int(om0[0]), len(a))], [(2, b)])
+    assert np.array_equal(la0[0], lm0[0])
+    assert np.array_equal(la1[0], lm1[0])  # decode row next to a prompt
+    assert np.array_equal(lb[0], lm1[1])   # prompt next to a decode row
 
 
 def test_server_serves_a_workload_with_rekeys(cloak_lib):
