@@ -102,16 +102,35 @@ class ClockSampler:
 
 # ------------------------------------------------------------- distributed
 
-def dist_setup():
+def dist_setup(backend: str = "nccl"):
+    """One process per GPU (RANK / LOCAL_RANK / WORLD_SIZE / MASTER_* from the
+    launcher). The path shards by independent problems: every rank keys and
+    runs its own context; the only collectives are the barrier and the max of
+    the timings. backend "gloo" runs the same rank logic on CPU."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     if ws == 1:
         return 0, 1, 0
     import torch
     import torch.distributed as dist
     rank, local = int(os.environ["RANK"]), int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    if backend == "nccl":
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    else:
+        dist.init_process_group(backend)
     return rank, ws, local
+
+
+def rank_key(rank: int) -> int:
+    """Each GPU shuffles its own copy under its own key (the paper shuffles
+    independently per GPU)."""
+    return KEY + rank
+
+
+def job_rate(units_per_rank: float, ms_max: float, ws: int) -> float:
+    """Whole-job throughput: the units every rank processed over the slowest
+    rank's time (weak scaling: each rank does the same work)."""
+    return units_per_rank * ws / (ms_max / 1e3)
 
 
 def max_over_ranks(v: float, ws: int) -> float:
@@ -119,7 +138,8 @@ def max_over_ranks(v: float, ws: int) -> float:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cpu" if dist.get_backend() == "gloo" else "cuda"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -385,7 +405,7 @@ def run_cloak(args):
     cm = cloak.CloakModel(model, device=dev, twin=True)
 
     t0 = time.perf_counter()
-    cm.keygen(KEY + rank, 0)
+    cm.keygen(rank_key(rank), 0)
     keygen_ms = (time.perf_counter() - t0) * 1e3
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -452,7 +472,7 @@ def run_cloak(args):
     ms = time_graph(g_cl, args.steps, args.warmup)
     ms_un = time_graph(g_un, args.steps, args.warmup)
     B = step_bytes(model, M)
-    value = B / (ms / 1e3) / 1e9 * ws
+    value = job_rate(B, ms, ws) / 1e9
 
     # kernel duration for the roofline: a GPU-side sleep lets the host queue
     # every launch and event first, so the launches run back to back
@@ -540,7 +560,7 @@ def run_cloak(args):
     rk = []
     for e in range(1, 4):
         a.record()
-        cm.rekey(KEY + rank, e)
+        cm.rekey(rank_key(rank), e)
         b.record()
         torch.cuda.synchronize()
         rk.append(a.elapsed_time(b))
@@ -548,7 +568,7 @@ def run_cloak(args):
     moved = cm.NP * model.page_bytes
     status = cm.device_status()
     cm.close()
-    extras = None if args.no_extras else bench_extras(cloak, synth, torch, dev, stream, KEY + rank,
+    extras = None if args.no_extras else bench_extras(cloak, synth, torch, dev, stream, rank_key(rank),
                                                       args.steps, tune=not args.no_tune)
     clk = clocks.stop()
 
@@ -576,12 +596,12 @@ def run_cloak(args):
                          "kernel": "k_linear_tc<bf16, N=16>: one launch, 7 linears, swap-AB tcgen05, stream-K",
                          "kernel_us": round(kern_ms * 1e3, 2)},
             "cpu_baseline": cpu,
-            "e2e": {"value": round(B / (e2e_ms / 1e3) / 1e9 * ws, 2), "unit": "GB/s",
+            "e2e": {"value": round(job_rate(B, e2e_ms, ws) / 1e9, 2), "unit": "GB/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": e2e_ms, "api": "cloak_linear_batch_host (7 linears; inputs and outputs packed in pinned host buffers)"},
             "clocks": clk,
             "gpu_launches": launches_per_step * args.steps,
-            "uncloaked": {"value": round(B / (ms_un / 1e3) / 1e9 * ws, 1), "ms_per_step": ms_un,
+            "uncloaked": {"value": round(job_rate(B, ms_un, ws) / 1e9, 1), "ms_per_step": ms_un,
                           "overhead_pct": round((ms / ms_un - 1) * 100, 2)},
             "sweep_batch": sweep,
             "separate_launches_us": [round(v, 2) for v in per_tensor_us],
