@@ -673,6 +673,7 @@ def run_profile(args):
     """Small cases of one kernel each, for ncu captures (a few GB at most):
     stack  -- a 4-layer 7B-class stack (1.6 GB), decode M=1, 3 launches;
     fp8    -- one GQA E4M3 layer (233 MB), grouped decode M=1, 3 launches;
+    fp8prefill -- the same layer, grouped prefill M=2048 (the prefill GEMM), 3 launches;
     prefill-- one 7B-class layer, grouped M=2048 (the prefill GEMM), 3 launches;
     decode -- one 7B-class layer, grouped M=1 (the headline step), 3 launches.
     The linears' launch shape is tuned first (unless --no-tune); the profiled
@@ -684,7 +685,7 @@ def run_profile(args):
     torch.cuda.set_device(0)
     if args.profile == "stack":
         model = synth.llama7b_layer(4)
-    elif args.profile == "fp8":
+    elif args.profile in ("fp8", "fp8prefill"):
         model = synth.gqa28_fp8(1)
     else:
         model = synth.llama7b_layer(1)
@@ -701,7 +702,7 @@ def run_profile(args):
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
     else:
-        M = 2048 if args.profile == "prefill" else 1
+        M = 2048 if args.profile in ("prefill", "fp8prefill") else 1
         xs = [torch.from_numpy(synth.activations_host(M, t.k, seed=i)).cuda().to(torch.bfloat16)
               for i, t in enumerate(model.tensors)]
         group = list(range(len(model.tensors)))
@@ -730,7 +731,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--serve", action="store_true", help="run the serving sweep instead")
-    ap.add_argument("--profile", choices=["stack", "fp8", "prefill", "decode"],
+    ap.add_argument("--profile", choices=["stack", "fp8", "fp8prefill", "prefill", "decode"],
                     help="small case for ncu")
     ap.add_argument("--rates", default="2,8,32")
     ap.add_argument("--serve-seconds", type=float, default=30.0)

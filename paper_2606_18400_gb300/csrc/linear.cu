@@ -106,14 +106,37 @@ struct QuantJobs {
 };
 
 // one launch for every problem of a batch: block (r, p) quantises row r of x_p
-__global__ void k_quant_rows_multi(QuantJobs j) {
+__global__ void __launch_bounds__(256) k_quant_rows_multi(QuantJobs j) {
     griddep_launch_dependents();  // the linear may start (and fetch weights) now
     const int p = blockIdx.y;
     const int64_t r = blockIdx.x;
     const int K = j.K[p];
     const __nv_bfloat16 *xr = j.x[p] + r * K;
+    uint8_t *qr = j.q[p] + r * K;
+    // rows of up to 256 threads x 8 x VR values are read once, 16 bytes per
+    // load, into registers; other rows take the scalar loop twice
+    constexpr int VR = 12;
+    const bool vec = (K % 8) == 0 && K <= 256 * 8 * VR;
+    uint4 w[VR];
     float m = 0.0f;
-    for (int c = threadIdx.x; c < K; c += blockDim.x) m = fmaxf(m, fabsf(__bfloat162float(xr[c])));
+    if (vec) {
+#pragma unroll
+        for (int i = 0; i < VR; ++i) {
+            const int k = (i * 256 + (int)threadIdx.x) * 8;
+            w[i] = k < K ? __ldg(reinterpret_cast<const uint4 *>(xr + k)) : make_uint4(0u, 0u, 0u, 0u);
+        }
+#pragma unroll
+        for (int i = 0; i < VR; ++i) {
+            const __nv_bfloat162 *h2 = reinterpret_cast<const __nv_bfloat162 *>(&w[i]);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float2 f = __bfloat1622float2(h2[e]);
+                m = fmaxf(m, fmaxf(fabsf(f.x), fabsf(f.y)));
+            }
+        }
+    } else {
+        for (int c = threadIdx.x; c < K; c += blockDim.x) m = fmaxf(m, fabsf(__bfloat162float(xr[c])));
+    }
     __shared__ float red[32];
     __shared__ float sc;
     for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -129,10 +152,27 @@ __global__ void k_quant_rows_multi(QuantJobs j) {
     }
     __syncthreads();
     const float d = sc;
-    uint8_t *qr = j.q[p] + r * K;
-    for (int c = threadIdx.x; c < K; c += blockDim.x)
-        qr[c] = (uint8_t)__nv_cvt_float_to_fp8(__fdiv_rn(__bfloat162float(xr[c]), d), __NV_SATFINITE,
-                                                __NV_E4M3);
+    if (vec) {
+#pragma unroll
+        for (int i = 0; i < VR; ++i) {
+            const int k = (i * 256 + (int)threadIdx.x) * 8;
+            if (k >= K) continue;
+            const __nv_bfloat162 *h2 = reinterpret_cast<const __nv_bfloat162 *>(&w[i]);
+            uint32_t q[2] = {0u, 0u};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float2 f = __bfloat1622float2(h2[e]);
+                const uint32_t lo = __nv_cvt_float_to_fp8(__fdiv_rn(f.x, d), __NV_SATFINITE, __NV_E4M3);
+                const uint32_t hi = __nv_cvt_float_to_fp8(__fdiv_rn(f.y, d), __NV_SATFINITE, __NV_E4M3);
+                q[e >> 1] |= (lo | (hi << 8)) << ((e & 1) * 16);
+            }
+            *reinterpret_cast<uint2 *>(qr + k) = make_uint2(q[0], q[1]);
+        }
+    } else {
+        for (int c = threadIdx.x; c < K; c += blockDim.x)
+            qr[c] = (uint8_t)__nv_cvt_float_to_fp8(__fdiv_rn(__bfloat162float(xr[c]), d), __NV_SATFINITE,
+                                                    __NV_E4M3);
+    }
 }
 
 // ------------------------------------------------------ tensor-core path
