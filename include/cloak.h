@@ -86,7 +86,19 @@ typedef struct {
     int32_t n_units, unit, parent, ratio;
 } cloak_group_desc;
 
-enum { CLOAK_MODEL_TWIN = 1 };  /* also keep an uncloaked tile-major copy */
+enum {
+    CLOAK_MODEL_TWIN = 1,  /* also keep an uncloaked tile-major copy          */
+    CLOAK_MODEL_VMM = 2    /* Section 4.2 physical page remapping through CUDA
+                              virtual memory management: every arena page is
+                              its own physical chunk (cuMemCreate), mapped at
+                              its physical position in the arena and, in a
+                              second address range (the virtual view), at
+                              virtual page vp -> chunk page_alloc[vp]. The two
+                              views alias: no extra memory. page_bytes must be
+                              a multiple of the VMM allocation granularity
+                              (2 MiB), else cloak_create fails with
+                              CLOAK_E_UNSUPPORTED. See CLOAK_LINEAR_VMM.     */
+};
 
 typedef struct {
     int32_t num_tensors, num_groups;
@@ -98,7 +110,7 @@ typedef struct {
     int32_t spare_pages;     /* extra physical pages left free in the arena   */
     int32_t tile_scope;      /* 0: one tile permutation over the model;
                                 1: one per tensor (layers still shuffled)     */
-    int32_t flags;           /* CLOAK_MODEL_TWIN                              */
+    int32_t flags;           /* CLOAK_MODEL_TWIN | CLOAK_MODEL_VMM            */
     int64_t page_bytes;      /* page size, a multiple of the tile bytes       */
 } cloak_model_desc;
 
@@ -155,13 +167,24 @@ CLOAK_API cloak_status cloak_unshuffle(const cloak_ctx *ctx, int32_t tensor, voi
 CLOAK_API cloak_status cloak_scales(const cloak_ctx *ctx, int32_t tensor, const float **dev_out);
 
 /* Device pointer to the arena and its size in bytes (for audits and tests;
- * owned by the context). which = 0 arena, 1 twin. */
+ * owned by the context). which = 0 arena, 1 twin, 2 the virtual view of a
+ * CLOAK_MODEL_VMM context (NP pages; valid once keyed, and its pointer does
+ * not change across re-keys; the pages behind it do). */
 CLOAK_API cloak_status cloak_arena(const cloak_ctx *ctx, int32_t which, void **dev_out, int64_t *bytes);
 
 enum {
     CLOAK_LINEAR_UNCLOAKED = 1,  /* run the same kernel on the twin, tiles
                                     addressed arithmetically (tile-major)    */
-    CLOAK_LINEAR_RELU = 2        /* y = max(y, 0)                             */
+    CLOAK_LINEAR_RELU = 2,       /* y = max(y, 0)                             */
+    CLOAK_LINEAR_VMM = 8         /* CLOAK_MODEL_VMM contexts: run the same
+                                    kernel on the virtual view, each tile
+                                    found at its virtual position (the tile
+                                    permutation); the MMU supplies the page
+                                    map. Same tiles, same summation order:
+                                    bit for bit the result of the arena
+                                    read. Not with CLOAK_LINEAR_UNCLOAKED, and
+                                    CLOAK_E_STATE while a concurrent re-key
+                                    is in progress.                          */
 };
 enum { CLOAK_OUT_F32 = 0, CLOAK_OUT_BF16 = 1 };
 
@@ -355,6 +378,16 @@ CLOAK_API cloak_status cloak_tune_clear(cloak_ctx *ctx);
  * returns. Linear calls must not run concurrently with the moves: order them
  * on the same stream or with events. */
 CLOAK_API cloak_status cloak_rekey(cloak_ctx *ctx, uint64_t key, uint32_t new_epoch, void *stream);
+
+/* CLOAK_MODEL_VMM contexts: cloak_keygen, cloak_rekey and the last
+ * cloak_rekey_advance (the one that sets *done = 1) end with the remap of the
+ * virtual view to the new page map. The remap is a sync point: it
+ * synchronises the device (nothing may read the view while a page is
+ * unmapped), then unmaps and maps each virtual page whose chunk changed
+ * (cuMemUnmap, cuMemMap, cuMemSetAccess). out[0] = pages changed by the last
+ * remap, out[1] = remaps so far, out[2] = chunks (arena pages incl. staging).
+ * CLOAK_E_STATE for a context without CLOAK_MODEL_VMM. */
+CLOAK_API cloak_status cloak_vmm_stats(const cloak_ctx *ctx, int64_t out[3]);
 
 /* Concurrent re-key: the same moves as cloak_rekey, made while the model
  * keeps serving. The remap of Section 4.2 pauses execution at a sync point;

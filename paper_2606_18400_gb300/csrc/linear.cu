@@ -724,13 +724,12 @@ int tc_npad(int m) { return m <= 16 ? 16 : m <= 32 ? 32 : m <= 64 ? 64 : m <= 12
 cloak_status linear_batch_run(cloak_ctx *ctx, int n, const int32_t *tensors, const void *const *xs,
                               void *const *ys, int M, int out_dtype, int flags, cudaStream_t s) {
     CLOAK_CUDA(ctx, cudaSetDevice(ctx->device));
-    const bool unc = flags & CLOAK_LINEAR_UNCLOAKED;
     const int relu = (flags & CLOAK_LINEAR_RELU) ? 1 : 0;
-    const uint32_t *slot_of = unc ? nullptr : ctx->d_tile_slot;
+    const uint32_t *slot_of = weight_slots(ctx, flags);
     const int oes = out_dtype == CLOAK_OUT_F32 ? 4 : 2;
     if (ctx->dtype == CLOAK_F32) {
         if (ctx->tile_r != 64 || ctx->tile_c != 64) return CLOAK_E_UNSUPPORTED;
-        const uint8_t *arena = unc ? ctx->twin : ctx->arena;
+        const uint8_t *arena = weight_base(ctx, flags);
         for (int p = 0; p < n; ++p) {
             const TensorInfo &ti = ctx->info[tensors[p]];
             k_linear_f32<8><<<ti.nt, 256, 0, s>>>(arena, slot_of, ctx->h_tensor_base[tensors[p]], ti.n,
@@ -741,7 +740,7 @@ cloak_status linear_batch_run(cloak_ctx *ctx, int n, const int32_t *tensors, con
         return CLOAK_OK;
     }
     const bool fp8 = ctx->dtype == CLOAK_E4M3;
-    const CUtensorMap &tw = unc ? ctx->tmap_twin : ctx->tmap_arena;
+    const CUtensorMap &tw = weight_map(ctx, flags);
     // launch shape: forced (tuner measuring), tuned, or the default
     TuneCfg cfg = tune_lookup(ctx, n, tensors, M, out_dtype);
     if (ctx->tune_invariant) cfg.grid = 0;  // the split over CTAs fixes the summation order
@@ -787,8 +786,7 @@ cloak_status linear_batch_run(cloak_ctx *ctx, int n, const int32_t *tensors, con
         } else {
             for (int p = 0; p < n; ++p) xg[p] = xs[p];
         }
-        const CUtensorMap &twg = unc ? ctx->tmap_twin : ctx->tmap_arena;
-        return gemm_run(ctx, n, tensors, xg, sg, ys, M, out_dtype == CLOAK_OUT_F32, relu, slot_of, twg, s);
+        return gemm_run(ctx, n, tensors, xg, sg, ys, M, out_dtype == CLOAK_OUT_F32, relu, slot_of, tw, s);
     }
     // E4M3 decode batches quantise their activations inside the linear (each
     // CTA for the problems it touches); this needs K a multiple of 16

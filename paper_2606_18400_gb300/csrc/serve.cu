@@ -41,9 +41,8 @@ static cloak_status step_linears(cloak_ctx *ctx, int n, const int32_t *ts, const
             xp[i] = (const uint8_t *)xs[i] + (size_t)m_dec * ti.k * 2;
             yp[i] = (uint8_t *)ys[i] + (size_t)m_dec * ti.n * oes;
         }
-        const bool unc = flags & CLOAK_LINEAR_UNCLOAKED;
         rc = gemm_run(ctx, n, ts, xp, nullptr, yp, M - m_dec, out_dtype == CLOAK_OUT_F32, 0,
-                      unc ? nullptr : ctx->d_tile_slot, unc ? ctx->tmap_twin : ctx->tmap_arena, s);
+                      weight_slots(ctx, flags), weight_map(ctx, flags), s);
     }
     return rc;
 }
@@ -508,7 +507,7 @@ static cloak_status serve_step_body(cloak_ctx *ctx, const cloak_serve_desc *d,
     if (d->lm_head < 0 || d->lm_head >= (int)ctx->tensors.size() || ctx->tensors[d->lm_head].n != V ||
         ctx->tensors[d->lm_head].k != D)
         return CLOAK_E_INVAL;
-    const int flags = (b->flags & CLOAK_LINEAR_UNCLOAKED);
+    const int flags = (b->flags & (CLOAK_LINEAR_UNCLOAKED | CLOAK_LINEAR_VMM));
     const int m_dec = (b->flags & CLOAK_SERVE_DECODE_FIRST) ? b->num_single : b->num_tokens;
     // workspace: h, y (fp32 [M, max(D, F)]), g, u (fp32 [M, F]), x, attn, q, k, v, act (bf16), logits
     const size_t Mz = (size_t)M;

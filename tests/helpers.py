@@ -11,11 +11,11 @@ def torch_bf16_bits(t):
     return t.contiguous().view(torch.int16).cpu().numpy().view(np.uint16)
 
 
-def place_both(cloak, model, key, epoch=0, seed=0, twin=True, weights=None):
+def place_both(cloak, model, key, epoch=0, seed=0, twin=True, weights=None, vmm=False):
     """Keygen + shuffle on the GPU and in the oracle with the same inputs.
     Returns (gpu model, oracle model, oracle tables, oracle arena, scales, Ws)."""
     import torch
-    cm = cloak.CloakModel(model, twin=twin)
+    cm = cloak.CloakModel(model, twin=twin, vmm=vmm)
     cm.keygen(key, epoch)
     Ws = weights if weights is not None else synth.weights_host(model, seed=seed)
     for t, W in enumerate(Ws):
