@@ -386,7 +386,84 @@ def bench_extras(cloak, synth, torch, dev, stream, key, steps, tune=True):
     assert cm.device_status() == 0
     cm.close()
     torch.cuda.empty_cache()
+    out["vmm_page_remap"] = bench_vmm(cloak, synth, torch, dev, stream, key, timed, graph, layer_run)
     return out
+
+
+def bench_vmm(cloak, synth, torch, dev, stream, key, timed, graph, layer_run):
+    """Section 4.2's physical page remapping through CUDA VMM: the arena's
+    2 MiB pages are separate physical chunks; the kernels read either the
+    arena (the gather table does the page step) or the virtual view (the
+    MMU does it). The same launches on both, and re-key + remap cost."""
+    res = {}
+    model = synth.llama7b_layer(1)
+    T, M = len(model.tensors), 1
+    xs = [torch.from_numpy(synth.activations_host(M, t.k, seed=600 + i)).cuda().to(torch.bfloat16)
+          for i, t in enumerate(model.tensors)]
+    ys = [torch.empty((M, t.n), dtype=torch.bfloat16, device="cuda") for t in model.tensors]
+    b1 = step_bytes(model, M)
+    lay = {}
+    # the same launches, tuned alike, on one cudaMalloc block (malloc) and on
+    # per-page chunks read through the arena (arena) or the view (view)
+    for vmm, runs in ((False, (("malloc", 0),)), (True, (("arena", 0), ("view", cloak.LINEAR_VMM)))):
+        cm = cloak.CloakModel(model, device=dev, vmm=vmm)
+        cm.keygen(key, 0)
+        for t in range(T):
+            cm.shuffle(t, synth.weights_device(model, t, seed=0))
+        cm.autotune(list(range(T)), xs, ys, out_dtype=cloak.OUT_BF16, stream=stream.cuda_stream)
+        for name, flags in runs:
+            def fn(flags=flags):
+                cloak.cloak_linear_batch(cm.ctx, list(range(T)), [x.data_ptr() for x in xs],
+                                         [y.data_ptr() for y in ys], M, cloak.OUT_BF16, flags,
+                                         stream.cuda_stream)
+            g = graph(fn)
+            ms = timed(g.replay, 400)
+            del g
+            lay[name + "_us"] = round(ms * 1e3, 2)
+            lay[name + "_gbs"] = round(b1 / (ms / 1e3) / 1e9, 1)
+        cm.close()
+        torch.cuda.empty_cache()
+    res["decode_llama7b_layer_M1"] = lay
+
+    model = synth.llama7b_layer(32)
+    cm = cloak.CloakModel(model, device=dev, vmm=True)
+    cm.keygen(key, 0)
+    res["keygen_remap_ms"] = round(cm.vmm_stats()["remap_us"] / 1e3, 2)
+    for t in range(len(model.tensors)):
+        w = synth.weights_device(model, t, seed=0)
+        cm.shuffle(t, w)
+        del w
+    torch.cuda.synchronize()
+    desc = cm.stack_desc()
+    stk = {}
+    for M in (1, 8):
+        h0 = torch.from_numpy(synth.activations_host(M, 4096, seed=M)).cuda()
+        row = {}
+        for name, vmm in (("arena", False), ("view", True)):
+            hb = h0.clone()
+            def fn(hb=hb, vmm=vmm):
+                hb.copy_(h0)
+                cm.stack_decode(hb, desc=desc, stream=stream.cuda_stream, vmm=vmm)
+            g2 = graph(fn)
+            row[name + "_ms"] = round(timed(g2.replay, 10), 4)
+            del g2
+        stk[str(M)] = row
+    res["stack_decode_llama7b_32L"] = stk
+    ts = []
+    for e in range(1, 4):
+        t0 = time.perf_counter()
+        cm.rekey(key, e)
+        torch.cuda.synchronize()
+        st = cm.vmm_stats()
+        ts.append(((time.perf_counter() - t0) * 1e3, st["remap_us"] / 1e3, st["pages_remapped"]))
+    res["rekey_llama7b_32L"] = {"rekey_and_remap_ms": round(statistics.median(x[0] for x in ts), 2),
+                                "remap_ms": round(statistics.median(x[1] for x in ts), 2),
+                                "pages_remapped": int(statistics.median(x[2] for x in ts)),
+                                "pages": cm.NP, "chunks": cm.vmm_stats()["chunks"]}
+    assert cm.device_status() == 0
+    cm.close()
+    torch.cuda.empty_cache()
+    return res
 
 
 def run_cloak(args):

@@ -385,9 +385,11 @@ CLOAK_API cloak_status cloak_rekey(cloak_ctx *ctx, uint64_t key, uint32_t new_ep
  * synchronises the device (nothing may read the view while a page is
  * unmapped), then unmaps and maps each virtual page whose chunk changed
  * (cuMemUnmap, cuMemMap, cuMemSetAccess). out[0] = pages changed by the last
- * remap, out[1] = remaps so far, out[2] = chunks (arena pages incl. staging).
- * CLOAK_E_STATE for a context without CLOAK_MODEL_VMM. */
-CLOAK_API cloak_status cloak_vmm_stats(const cloak_ctx *ctx, int64_t out[3]);
+ * remap, out[1] = remaps so far, out[2] = chunks (arena pages incl. staging),
+ * out[3] = host time of the last remap in microseconds, the device
+ * synchronisation included. CLOAK_E_STATE for a context without
+ * CLOAK_MODEL_VMM. */
+CLOAK_API cloak_status cloak_vmm_stats(const cloak_ctx *ctx, int64_t out[4]);
 
 /* Concurrent re-key: the same moves as cloak_rekey, made while the model
  * keeps serving. The remap of Section 4.2 pauses execution at a sync point;

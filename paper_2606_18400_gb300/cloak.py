@@ -324,9 +324,9 @@ class _DevArray:
 
 
 def cloak_vmm_stats(ctx) -> dict:
-    out = (C.c_int64 * 3)()
+    out = (C.c_int64 * 4)()
     _check("cloak_vmm_stats", load().cloak_vmm_stats(ctx, out), ctx)
-    return {"pages_remapped": out[0], "remaps": out[1], "chunks": out[2]}
+    return {"pages_remapped": out[0], "remaps": out[1], "chunks": out[2], "remap_us": out[3]}
 
 
 def _storage(uncloaked=False, vmm=False):

@@ -357,12 +357,13 @@ extern "C" cloak_status cloak_arena(const cloak_ctx *ctx, int32_t which, void **
     return CLOAK_OK;
 }
 
-extern "C" cloak_status cloak_vmm_stats(const cloak_ctx *ctx, int64_t out[3]) {
+extern "C" cloak_status cloak_vmm_stats(const cloak_ctx *ctx, int64_t out[4]) {
     if (!ctx || !out) return CLOAK_E_INVAL;
     if (!ctx->vview) return CLOAK_E_STATE;
     out[0] = ctx->vmm_remapped;
     out[1] = ctx->vmm_remaps;
     out[2] = (int64_t)ctx->vmm_chunks.size();
+    out[3] = ctx->vmm_remap_us;
     return CLOAK_OK;
 }
 

@@ -88,6 +88,7 @@ struct cloak_ctx {
     bool vmm_ready = false;                    // every virtual page mapped to the current page map
     std::vector<uint32_t> vmm_map;             // virtual page -> chunk mapped there (NONE: unmapped)
     int64_t vmm_remapped = 0, vmm_remaps = 0;  // pages changed by the last remap; remaps so far
+    int64_t vmm_remap_us = 0;                  // host time of the last remap
     CUtensorMap tmap_view{};
     float *d_scales = nullptr;
     int64_t scales_total = 0;

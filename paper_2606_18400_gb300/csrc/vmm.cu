@@ -18,6 +18,7 @@
 // this process reads a page while its mapping changes.
 #include <cudaTypedefs.h>
 
+#include <chrono>
 #include <mutex>
 
 #include "internal.cuh"
@@ -86,15 +87,12 @@ cloak_status drv_fail(cloak_ctx *ctx, CUresult r, const char *where) {
         if (r_ != CUDA_SUCCESS) return drv_fail(ctx, r_, where); \
     } while (0)
 
-cloak_status map_rw(cloak_ctx *ctx, CUdeviceptr va, uint32_t chunk) {
-    const VmmApi &a = api();
-    const size_t P = (size_t)ctx->page_bytes;
-    VMM_DRV(ctx, a.map(va, P, 0, ctx->vmm_chunks[chunk], 0), "cuMemMap");
+cloak_status set_rw(cloak_ctx *ctx, CUdeviceptr va, size_t bytes) {
     CUmemAccessDesc acc{};
     acc.location.type = CU_MEM_LOCATION_TYPE_DEVICE;
     acc.location.id = ctx->device;
     acc.flags = CU_MEM_ACCESS_FLAGS_PROT_READWRITE;
-    VMM_DRV(ctx, a.set_access(va, P, &acc, 1), "cuMemSetAccess");
+    VMM_DRV(ctx, api().set_access(va, bytes, &acc, 1), "cuMemSetAccess");
     return CLOAK_OK;
 }
 
@@ -127,10 +125,10 @@ cloak_status vmm_create(cloak_ctx *ctx, int64_t chunks) {
     ctx->vmm_phys_bytes = P * (size_t)chunks;
     ctx->arena = reinterpret_cast<uint8_t *>(pv);
     for (int64_t i = 0; i < chunks; ++i) {
-        cloak_status rc = map_rw(ctx, pv + (CUdeviceptr)(i * P), (uint32_t)i);
-        if (rc) return rc;
+        VMM_DRV(ctx, a.map(pv + (CUdeviceptr)(i * P), P, 0, ctx->vmm_chunks[i], 0), "cuMemMap");
         ctx->vmm_phys_mapped = i + 1;
     }
+    if (cloak_status rc = set_rw(ctx, pv, P * (size_t)chunks)) return rc;
     VMM_DRV(ctx, a.reserve(&vv, P * (size_t)ctx->NP, P, 0, 0), "cuMemAddressReserve");
     ctx->vview = reinterpret_cast<uint8_t *>(vv);
     ctx->vmm_map.assign((size_t)ctx->NP, NONE);
@@ -139,6 +137,7 @@ cloak_status vmm_create(cloak_ctx *ctx, int64_t chunks) {
 
 cloak_status vmm_remap(cloak_ctx *ctx) {
     const VmmApi &a = api();
+    const auto t0 = std::chrono::steady_clock::now();
     ctx->vmm_ready = false;  // until every page is mapped again
     // the sync point: nothing of this process may read the view while its
     // pages are unmapped
@@ -148,25 +147,40 @@ cloak_status vmm_remap(cloak_ctx *ctx) {
     const size_t P = (size_t)ctx->page_bytes;
     const CUdeviceptr vv = reinterpret_cast<CUdeviceptr>(ctx->vview);
     const uint32_t nch = (uint32_t)ctx->vmm_chunks.size();
-    int64_t changed = 0;
-    for (int64_t vp = 0; vp < ctx->NP; ++vp) {
+    for (int64_t vp = 0; vp < ctx->NP; ++vp)
         if (pa[vp] >= nch) {
             ctx->last_err = "page map entry out of range";
             return CLOAK_E_CUDA;
         }
-        if (ctx->vmm_map[vp] == pa[vp]) continue;
-        const CUdeviceptr va = vv + (CUdeviceptr)(vp * P);
-        if (ctx->vmm_map[vp] != NONE) {
-            VMM_DRV(ctx, a.unmap(va, P), "cuMemUnmap");
-            ctx->vmm_map[vp] = NONE;
+    // runs of consecutive virtual pages whose chunk changes: one unmap per
+    // run of mapped pages, one map per page, one access grant per run. A
+    // page's entry in vmm_map is written only once its run is accessible, so
+    // after a failure the view stays refused (vmm_ready false) and no entry
+    // claims a page that a kernel could not read.
+    int64_t changed = 0;
+    for (int64_t v0 = 0; v0 < ctx->NP;) {
+        if (ctx->vmm_map[v0] == pa[v0]) { ++v0; continue; }
+        int64_t v1 = v0;
+        while (v1 < ctx->NP && ctx->vmm_map[v1] != pa[v1]) ++v1;
+        for (int64_t u0 = v0; u0 < v1;) {
+            if (ctx->vmm_map[u0] == NONE) { ++u0; continue; }
+            int64_t u1 = u0;
+            while (u1 < v1 && ctx->vmm_map[u1] != NONE) ++u1;
+            VMM_DRV(ctx, a.unmap(vv + (CUdeviceptr)(u0 * P), (size_t)(u1 - u0) * P), "cuMemUnmap");
+            for (int64_t u = u0; u < u1; ++u) ctx->vmm_map[u] = NONE;
+            u0 = u1;
         }
-        cloak_status rc = map_rw(ctx, va, pa[vp]);
-        if (rc) return rc;
-        ctx->vmm_map[vp] = pa[vp];
-        ++changed;
+        for (int64_t v = v0; v < v1; ++v)
+            VMM_DRV(ctx, a.map(vv + (CUdeviceptr)(v * P), P, 0, ctx->vmm_chunks[pa[v]], 0), "cuMemMap");
+        if (cloak_status rc = set_rw(ctx, vv + (CUdeviceptr)(v0 * P), (size_t)(v1 - v0) * P)) return rc;
+        for (int64_t v = v0; v < v1; ++v) ctx->vmm_map[v] = pa[v];
+        changed += v1 - v0;
+        v0 = v1;
     }
     ctx->vmm_remapped = changed;
     ctx->vmm_remaps++;
+    ctx->vmm_remap_us = std::chrono::duration_cast<std::chrono::microseconds>(
+                            std::chrono::steady_clock::now() - t0).count();
     ctx->vmm_ready = true;
     return CLOAK_OK;
 }

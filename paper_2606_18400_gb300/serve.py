@@ -52,11 +52,16 @@ class ServedModel:
 
     def __init__(self, model: synth.Model, kv_blocks: int, max_blocks: int, key: int = 0x1234,
                  twin: bool = False, seed: int = 0, device: int = 0, rope_theta: float = 10000.0,
-                 weights=None):
+                 weights=None, vmm: bool = False):
+        """vmm: page-chunked arena (Section 4.2 physical page remapping); the
+        steps read the weights through the virtual view, except while a
+        concurrent re-key moves pages (the view is remapped at its end), when
+        they read the arena through the gather table."""
         import torch
         self.model = model
         self.device = device
-        self.cm = cloak.CloakModel(model, device=device, twin=twin)
+        self.vmm, self._rekeying = vmm, False
+        self.cm = cloak.CloakModel(model, device=device, twin=twin, vmm=vmm)
         self.key = key
         self.epoch = 0
         self.cm.keygen(key, 0)
@@ -90,6 +95,8 @@ class ServedModel:
         nq = int(qtiles.shape[0]) if qtiles is not None else 0
         ns = int(single_rows.numel()) if single_rows is not None else 0
         flags = (cloak.LINEAR_UNCLOAKED if uncloaked else 0) | (cloak.SERVE_DECODE_FIRST if decode_first else 0)
+        if self.vmm and not uncloaked and not self._rekeying:
+            flags |= cloak.LINEAR_VMM
         b = cloak.ServeBatch(int(token_ids.numel()), int(sample_rows.numel()),
                              flags, token_ids.data_ptr(),
                              positions.data_ptr(), req_slots.data_ptr(), block_tables.data_ptr(),
@@ -107,10 +114,13 @@ class ServedModel:
         """Start a concurrent re-key to the next epoch (copies on `side_stream`)."""
         self.epoch += 1
         self.cm.rekey_begin(self.key, self.epoch, side_stream)
+        self._rekeying = True
 
     def rekey_advance(self, serve_stream, side_stream) -> bool:
         """At a step boundary: publish the landed wave, start the next; True when done."""
-        return self.cm.rekey_advance(serve_stream, side_stream)
+        done = self.cm.rekey_advance(serve_stream, side_stream)
+        self._rekeying = not done
+        return done
 
     def close(self):
         self.cm.close()

@@ -12,9 +12,9 @@ from paper_2606_18400_gb300 import cloak, serve, synth
 pytestmark = pytest.mark.gpu
 
 
-def small_served(layers=2):
+def small_served(layers=2, page_bytes=None):
     m = synth.small_decoder(layers, synth.DT_BF16, d_model=512, n_heads=4, n_kv_heads=2, d_ff=384,
-                            head_dim=128, spare_pages=3)
+                            head_dim=128, spare_pages=3, page_bytes=page_bytes)
     return synth.with_lm_head(m, 1000)
 
 
@@ -193,4 +193,28 @@ def test_server_serves_a_workload_with_rekeys(cloak_lib):
         assert sm.cm.device_status() == 0
         sm.close()
     # continuous batching and re-keys (between steps or concurrent) do not change results
+    assert outs[0] == outs[1] == outs[2]
+
+
+def test_server_on_the_vmm_view(cloak_lib):
+    """Served through the virtual view of a page-chunked arena (Section 4.2
+    physical page remapping), with re-keys between steps and concurrent ones
+    (the steps read the arena while pages move, the view again once it is
+    remapped): the same tokens as the arena read."""
+    m = small_served(page_bytes=2 << 20)
+    Ws = synth.weights_host(m, seed=0, std=0.05)
+    work = [(0.01 * i, np.random.default_rng(30 + i).integers(0, 1000, 25 + 9 * i).astype(np.int32), 3 + i % 4)
+            for i in range(8)]
+    outs = []
+    for vmm, conc in ((False, True), (True, True), (True, False)):
+        sm = serve.ServedModel(m, kv_blocks=128, max_blocks=16, weights=Ws, vmm=vmm)
+        srv = serve.Server(sm, max_running=4, token_budget=64, rekey_period=0.02, rekey_concurrent=conc)
+        done, wall = srv.run(work)
+        assert len(done) == 8 and len(srv.rekeys) >= 1
+        outs.append({r.rid: r.out for r in done})
+        if vmm:
+            assert sm.cm.vmm_stats()["remaps"] == 1 + len(srv.rekeys)
+            assert not sm._rekeying
+        assert sm.cm.device_status() == 0
+        sm.close()
     assert outs[0] == outs[1] == outs[2]

@@ -42,6 +42,7 @@ def test_views_hold_the_oracle_layout(cloak_lib, dtype):
     assert cm.NP >= 4
     st = cm.vmm_stats()
     assert st["chunks"] > cm.NPS and st["remaps"] == 1 and st["pages_remapped"] == cm.NP
+    assert st["remap_us"] > 0
     phys = cm.arena_bytes(0).cpu().numpy()
     assert np.array_equal(phys, arena)
     view = cm.arena_bytes(2).cpu().numpy()
