@@ -162,6 +162,25 @@ CLOAK_API cloak_status cloak_shuffle(cloak_ctx *ctx, int32_t tensor, const float
 CLOAK_API cloak_status cloak_unshuffle(const cloak_ctx *ctx, int32_t tensor, void *logical_dev,
                              int32_t from_twin, void *stream);
 
+/* Keyed upload (Section 5, "Implementation Details": the permutation is
+ * drawn and the physical pages allocated before any weight is transferred,
+ * so the bus never carries a structured layout). w_host[t] is tensor t's
+ * logical FP32 matrix [n, k], row-major, in host memory (pageable or pinned),
+ * for every tensor of the model. The host assembles each assigned arena page
+ * (permuted, converted, tiled and placed exactly as cloak_shuffle does) and
+ * copies it to the device whole; pages go in ascending physical order, runs
+ * of consecutive pages in one copy, through two pinned staging buffers of at
+ * most 64 MiB (kept by the context). The call also holds host memory of the
+ * model's tile bytes (the tiles in logical order, assembled first). E4M3 scales are computed on the host and uploaded after the
+ * pages. The arena afterwards equals cloak_shuffle of every tensor, bit for
+ * bit. threads: host threads assembling pages (0: the hardware's, at most
+ * 16). Synchronous (returns when the copies have landed). Errors:
+ * CLOAK_E_STATE before a keygen, during a concurrent re-key, or on a context
+ * with a twin (the twin is in logical order: filling it would put the
+ * logical layout on the bus). */
+CLOAK_API cloak_status cloak_upload(cloak_ctx *ctx, const float *const *w_host, int32_t threads,
+                                    void *stream);
+
 /* Device pointer to tensor `tensor`'s FP32 scales [n] in stored-row order
  * (E4M3 models only; owned by the context). */
 CLOAK_API cloak_status cloak_scales(const cloak_ctx *ctx, int32_t tensor, const float **dev_out);

@@ -165,6 +165,8 @@ static void release(cloak_ctx *c) {
     F(c->twin); F(c->d_scales); F(c->d_part); F(c->d_rowcnt); F(c->d_xq);
     F(c->d_xs); F(c->d_xstage); F(c->d_ystage); F(c->d_plan); F(c->d_status);
     F(c->d_stack_ws); F(c->d_serve_ws); F(c->rk.d_owner); F(c->d_xqp); F(c->d_xsg); F(c->d_gemm_next);
+    for (auto &h : c->h_upload_stage)
+        if (h) cudaFreeHost(h);
     if (c->rk.copied) cudaEventDestroy(c->rk.copied);
     if (c->rk.published) cudaEventDestroy(c->rk.published);
     KeygenWork &w = c->kw;
@@ -355,6 +357,16 @@ extern "C" cloak_status cloak_arena(const cloak_ctx *ctx, int32_t which, void **
     *dev_out = which == 2 ? ctx->vview : which ? ctx->twin : ctx->arena;
     *bytes = which == 2 ? ctx->NP * ctx->page_bytes : which ? ctx->twin_bytes : ctx->arena_bytes;
     return CLOAK_OK;
+}
+
+extern "C" cloak_status cloak_upload(cloak_ctx *ctx, const float *const *w_host, int32_t threads,
+                                     void *stream) {
+    if (!ctx || !w_host || threads < 0) return CLOAK_E_INVAL;
+    for (size_t t = 0; t < ctx->tensors.size(); ++t)
+        if (!w_host[t]) return CLOAK_E_INVAL;
+    if (!ctx->keyed || ctx->rk.active || ctx->twin) return CLOAK_E_STATE;
+    CLOAK_CUDA(ctx, cudaSetDevice(ctx->device));
+    return upload_run(ctx, w_host, threads, (cudaStream_t)stream);
 }
 
 extern "C" cloak_status cloak_vmm_stats(const cloak_ctx *ctx, int64_t out[4]) {

@@ -107,6 +107,8 @@ struct cloak_ctx {
     size_t xsg_cap = 0;
     void *d_gemm_next = nullptr;               // prefill tile counter
     void *d_xstage = nullptr, *d_ystage = nullptr;  // host-call staging
+    uint8_t *h_upload_stage[2] = {nullptr, nullptr};  // pinned keyed-upload staging
+    size_t upload_stage_bytes = 0;
     size_t xstage_cap = 0, ystage_cap = 0;
     uint8_t *d_stage = nullptr;                // re-key staging pages (arena pages
     int32_t stage_pages = 0;                   // NPS.., never assigned by a key)
@@ -178,6 +180,9 @@ cloak_status launch_unshuffle(const cloak_ctx *ctx, int t, void *dst, int from_t
 cloak_status rekey_run(cloak_ctx *ctx, uint64_t key, uint32_t new_epoch, cudaStream_t s);
 cloak_status rekey_begin(cloak_ctx *ctx, uint64_t key, uint32_t new_epoch, cudaStream_t side);
 cloak_status rekey_advance(cloak_ctx *ctx, cudaStream_t serve, cudaStream_t side, int32_t *done);
+
+// upload.cu
+cloak_status upload_run(cloak_ctx *ctx, const float *const *w, int threads, cudaStream_t s);
 
 // vmm.cu
 cloak_status vmm_create(cloak_ctx *ctx, int64_t chunks);
