@@ -50,7 +50,7 @@ class _Model(C.Structure):
     _fields_ = [("num_tensors", C.c_int32), ("num_groups", C.c_int32),
                 ("tensors", C.POINTER(_Tensor)), ("groups", C.POINTER(_Group)),
                 ("dtype", C.c_int32), ("tile_r", C.c_int32), ("tile_c", C.c_int32),
-                ("spare_pages", C.c_int32), ("tile_scope", C.c_int32), ("reserved", C.c_int32),
+                ("spare_pages", C.c_int32), ("tile_scope", C.c_int32), ("tile_rekey", C.c_int32),
                 ("page_bytes", C.c_int64)]
 
 
@@ -88,6 +88,7 @@ def lib():
         L.orc_stored_codes.argtypes = [C.POINTER(_Model), C.POINTER(_Tables), C.c_int, vp, vp, vp]
         L.orc_axis_maps.argtypes = [C.POINTER(_Model), C.POINTER(_Tables), C.c_int, vp, vp]
         L.orc_rekey.argtypes = [C.POINTER(_Model), C.POINTER(_Tables), C.POINTER(_Tables), vp, vp]
+        L.orc_rekey_tiles.argtypes = [C.POINTER(_Model), C.POINTER(_Tables), C.POINTER(_Tables), vp, vp]
         L.orc_bf16_encode.restype = C.c_uint16
         L.orc_bf16_encode.argtypes = [C.c_float]
         L.orc_bf16_decode.restype = C.c_float
@@ -120,7 +121,8 @@ class OracleModel:
         self._g = (_Group * max(Gn, 1))(*[_Group(g.n_units, g.unit, g.parent, g.ratio)
                                           for g in model.groups])
         self.c = _Model(T, Gn, self._t, self._g, model.dtype, model.tile_r, model.tile_c,
-                        model.spare_pages, model.tile_scope, 0, model.page_bytes)
+                        model.spare_pages, model.tile_scope, int(getattr(model, "tile_rekey", False)),
+                        model.page_bytes)
         geo = np.zeros(8, np.int64)
         rc = lib().orc_geometry(C.byref(self.c), _ptr(geo))
         if rc:
@@ -254,6 +256,14 @@ def rekey(om: OracleModel, old: Tables, new: Tables, arena: np.ndarray):
     tmp = np.empty_like(arena)
     assert lib().orc_rekey(C.byref(om.c), C.byref(_ctables(om, old)), C.byref(_ctables(om, new)),
                            _ptr(arena), _ptr(tmp)) == 0
+
+
+def rekey_tiles(om: OracleModel, old: Tables, new: Tables, arena: np.ndarray):
+    """Tile-level re-key (models with tile_rekey): every tile from its old
+    slot to its new one, the new map's empty slots zeroed (in place)."""
+    tmp = np.empty_like(arena)
+    assert lib().orc_rekey_tiles(C.byref(om.c), C.byref(_ctables(om, old)), C.byref(_ctables(om, new)),
+                                 _ptr(arena), _ptr(tmp)) == 0
 
 
 # ------------------------------------------------------------ number formats

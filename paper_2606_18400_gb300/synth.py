@@ -58,6 +58,7 @@ class Model:
     tensors: List[Tensor] = field(default_factory=list)
     groups: List[Group] = field(default_factory=list)
     tile_scope: int = 0    # 0: one tile permutation over the whole model; 1: per tensor
+    tile_rekey: bool = False  # redraw the tile permutation at every epoch (re-keys move tiles)
     # architecture constants used by the layer-stack/serving path
     d_model: int = 0
     n_heads: int = 0
