@@ -388,7 +388,39 @@ def bench_extras(cloak, synth, torch, dev, stream, key, steps, tune=True):
     torch.cuda.empty_cache()
     out["vmm_page_remap"] = bench_vmm(cloak, synth, torch, dev, stream, key, timed, graph, layer_run)
     out["keyed_upload_llama7b_layer"] = bench_upload(cloak, synth, torch, dev, key)
+    out["tile_rekey_llama7b_32L"] = bench_tile_rekey(cloak, synth, torch, dev, stream, key)
     return out
+
+
+def bench_tile_rekey(cloak, synth, torch, dev, stream, key):
+    """Tile-level re-key of the 32-layer stack: a new tile permutation and
+    page map, every 32 KiB tile moved to its new slot in place."""
+    model = synth.llama7b_layer(32)
+    model.tile_rekey = True
+    cm = cloak.CloakModel(model, device=dev)
+    cm.keygen(key, 0)
+    for t in range(len(model.tensors)):
+        w = synth.weights_device(model, t, seed=0)
+        cm.shuffle(t, w)
+        del w
+    torch.cuda.synchronize()
+    ts = []
+    for e in range(1, 4):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        a.record(stream)
+        cm.rekey(key, e, stream=stream.cuda_stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ts.append((a.elapsed_time(b), (time.perf_counter() - t0) * 1e3))
+    moved = cm.G * cm.tile_bytes
+    med = statistics.median(x[0] for x in ts)
+    res = {"ms": round(med, 3), "host_ms": round(statistics.median(x[1] for x in ts), 3),
+           "moved_bytes": moved, "gbs_rw": round(2 * moved / (med / 1e3) / 1e9, 1), "tiles": cm.G}
+    assert cm.device_status() == 0
+    cm.close()
+    torch.cuda.empty_cache()
+    return res
 
 
 def bench_upload(cloak, synth, torch, dev, key):

@@ -88,7 +88,7 @@ typedef struct {
 
 enum {
     CLOAK_MODEL_TWIN = 1,  /* also keep an uncloaked tile-major copy          */
-    CLOAK_MODEL_VMM = 2    /* Section 4.2 physical page remapping through CUDA
+    CLOAK_MODEL_VMM = 2,   /* Section 4.2 physical page remapping through CUDA
                               virtual memory management: every arena page is
                               its own physical chunk (cuMemCreate), mapped at
                               its physical position in the arena and, in a
@@ -98,6 +98,14 @@ enum {
                               a multiple of the VMM allocation granularity
                               (2 MiB), else cloak_create fails with
                               CLOAK_E_UNSUPPORTED. See CLOAK_LINEAR_VMM.     */
+    CLOAK_MODEL_TILE_REKEY = 4  /* the tile permutation is redrawn at every
+                              epoch too (its streams seeded with the epoch;
+                              epoch 0 draws what a model without the flag
+                              draws): cloak_rekey then moves every tile
+                              (32 KiB BF16, 16 KiB E4M3) to its slot under the
+                              new tables, so tiles also change pages and
+                              neighbours. Synchronous re-keys only:
+                              cloak_rekey_begin returns CLOAK_E_UNSUPPORTED. */
 };
 
 typedef struct {
@@ -110,7 +118,7 @@ typedef struct {
     int32_t spare_pages;     /* extra physical pages left free in the arena   */
     int32_t tile_scope;      /* 0: one tile permutation over the model;
                                 1: one per tensor (layers still shuffled)     */
-    int32_t flags;           /* CLOAK_MODEL_TWIN | CLOAK_MODEL_VMM            */
+    int32_t flags;           /* CLOAK_MODEL_TWIN | _VMM | _TILE_REKEY         */
     int64_t page_bytes;      /* page size, a multiple of the tile bytes       */
 } cloak_model_desc;
 

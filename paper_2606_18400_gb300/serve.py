@@ -136,7 +136,8 @@ class Server:
     default): the page copies run on a low-priority side stream while steps
     continue on the high-priority serving stream, and each landed wave is
     published between two steps; no step waits for a copy. With
-    `rekey_concurrent=False` the whole re-key runs between two steps."""
+    `rekey_concurrent=False`, or for a model whose re-keys move tiles
+    (`tile_rekey`), the whole re-key runs between two steps."""
 
     def __init__(self, sm: ServedModel, max_running: int = 64, token_budget: int = 2048,
                  rekey_period: Optional[float] = 30.0, uncloaked: bool = False,
@@ -144,7 +145,9 @@ class Server:
         import torch
         self.sm, self.uncloaked = sm, uncloaked
         self.max_running, self.budget = max_running, token_budget
-        self.rekey_period, self.rekey_concurrent = rekey_period, rekey_concurrent
+        # tile-level re-keys (models with tile_rekey) run between steps only
+        self.rekey_period = rekey_period
+        self.rekey_concurrent = rekey_concurrent and not getattr(sm.model, "tile_rekey", False)
         self.free_blocks = list(range(sm.kv_blocks))
         self.free_slots = list(range(max_running))
         dev = f"cuda:{sm.device}"
