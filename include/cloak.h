@@ -300,18 +300,23 @@ CLOAK_API cloak_status cloak_stack_decode(cloak_ctx *ctx, const cloak_stack_desc
                                           int32_t M, int32_t flags, void *stream);
 
 /* A served model: the decoder stack, a cloaked lm_head tensor [vocab,
- * d_model], a plain BF16 embedding table [vocab, d_model] (device, caller's)
- * and the paged KV cache (device, caller's): per layer, num_blocks blocks of
- * 16 tokens x n_kv_heads x 128, BF16, for keys and for values. */
+ * d_model], the embedding [vocab, d_model] -- either a cloaked tensor of the
+ * context (embed_tensor >= 0: its rows are looked up through the gather
+ * table, so the table is as hidden as the weights) or a plain BF16 table
+ * (embed_tensor = -1; device, caller's) -- and the paged KV cache (device,
+ * caller's): per layer, num_blocks blocks of 16 tokens x n_kv_heads x 128,
+ * BF16, for keys and for values. */
 typedef struct {
     cloak_stack_desc stack;
     int32_t lm_head;          /* tensor index of the output projection        */
     int32_t vocab;
-    const void *embedding;    /* BF16 [vocab, d_model]                          */
+    const void *embedding;    /* BF16 [vocab, d_model]; NULL with embed_tensor  */
     void *k_cache, *v_cache;  /* BF16 [layers][num_blocks][16][n_kv][128]       */
     int32_t num_blocks;
     int32_t max_blocks;       /* block-table row length (blocks per request)    */
     float rope_theta;
+    int32_t embed_tensor;     /* cloaked embedding tensor [vocab, d_model], not
+                                 permuted (a BF16 model), or -1                  */
 } cloak_serve_desc;
 
 /* One step's batch: num_tokens tokens of any requests (prefill chunks and
@@ -320,7 +325,8 @@ typedef struct {
  * positions 0..positions[m] through block_tables[req][pos / 16] (a request's
  * earlier positions must be in the cache or in this batch). sample_rows lists
  * the tokens whose next token is sampled (greedy) into out_tokens;
- * out_logits (FP32 [num_sample, vocab], may be NULL) receives their logits. */
+ * out_logits (FP32 [num_sample, vocab], may be NULL) receives their logits.
+ * A token id outside [0, vocab) embeds as a zero row. */
 /* cloak_serve_batch.flags, besides CLOAK_LINEAR_UNCLOAKED: the first
  * num_single tokens are the batch's decode tokens and the others prompt
  * tokens. The linears then run the decode rows through the split-K decode

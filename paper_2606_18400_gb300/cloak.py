@@ -59,7 +59,8 @@ class StackDesc(C.Structure):
 class ServeDesc(C.Structure):
     _fields_ = [("stack", StackDesc), ("lm_head", C.c_int32), ("vocab", C.c_int32),
                 ("embedding", C.c_void_p), ("k_cache", C.c_void_p), ("v_cache", C.c_void_p),
-                ("num_blocks", C.c_int32), ("max_blocks", C.c_int32), ("rope_theta", C.c_float)]
+                ("num_blocks", C.c_int32), ("max_blocks", C.c_int32), ("rope_theta", C.c_float),
+                ("embed_tensor", C.c_int32)]
 
 
 class TuneResult(C.Structure):

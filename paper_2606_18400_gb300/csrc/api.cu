@@ -535,7 +535,9 @@ extern "C" cloak_status cloak_stack_decode(cloak_ctx *ctx, const cloak_stack_des
 
 extern "C" cloak_status cloak_serve_step(cloak_ctx *ctx, const cloak_serve_desc *desc,
                                          const cloak_serve_batch *batch, void *stream) {
-    if (!ctx || !desc || !batch || !desc->stack.layer_tensors || !desc->embedding || !desc->k_cache ||
+    if (!ctx || !desc || !batch || !desc->stack.layer_tensors ||
+        (desc->embed_tensor < 0 ? !desc->embedding : desc->embed_tensor >= (int32_t)ctx->tensors.size()) ||
+        !desc->k_cache ||
         !desc->v_cache || desc->num_blocks <= 0 || desc->max_blocks <= 0 || desc->vocab <= 0 ||
         (batch->num_sample > 0 && (!batch->sample_rows || !batch->out_tokens)) ||
         (batch->flags & ~(CLOAK_LINEAR_UNCLOAKED | CLOAK_LINEAR_VMM | CLOAK_SERVE_DECODE_FIRST)) ||

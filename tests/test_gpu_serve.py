@@ -218,3 +218,38 @@ def test_server_on_the_vmm_view(cloak_lib):
         assert sm.cm.device_status() == 0
         sm.close()
     assert outs[0] == outs[1] == outs[2]
+
+
+@pytest.mark.parametrize("vmm", [False, True])
+def test_cloaked_embedding(cloak_lib, vmm):
+    """The embedding table as a cloaked tensor (looked up through the gather
+    table): the same logits as the plain BF16 table, bit for bit, through the
+    arena, the uncloaked twin and (page-chunked arena) the VMM view; and the
+    full-model oracle's logits within 1e-2."""
+    pb = (2 << 20) if vmm else None
+    plain = small_served(page_bytes=pb)
+    m = synth.small_decoder(2, synth.DT_BF16, d_model=512, n_heads=4, n_kv_heads=2, d_ff=384,
+                            head_dim=128, spare_pages=3, page_bytes=pb)
+    m = synth.with_lm_head(m, 1000, cloaked_embedding=True)
+    assert m.tensors[-1].kind == synth.K_EMBED and m.tensors[-1].layer == m.tensors[-2].layer + 1
+    Ws = synth.weights_host(plain, seed=0, std=0.05)
+    toks = list(np.random.default_rng(5).integers(0, 1000, 30))
+    a = serve.ServedModel(plain, kv_blocks=256, max_blocks=32, twin=not vmm, weights=Ws, vmm=vmm)
+    b = serve.ServedModel(m, kv_blocks=256, max_blocks=32, twin=not vmm, weights=Ws + [None], vmm=vmm)
+    assert b.embed_tensor == len(m.tensors) - 1 and b.embedding is None
+    la, sa = run_steps(a, [(0, toks)], tiled=True)
+    lb, sb = run_steps(b, [(0, toks)], tiled=True)
+    for x, y in zip(la[0], lb[0]):
+        assert np.array_equal(x, y)
+    assert sa == sb
+    if not vmm:
+        lu, su = run_steps(b, [(0, toks)], tiled=True, uncloaked=True)
+        for x, y in zip(la[0], lu[0]):
+            assert np.array_equal(x, y)
+    W64 = [O.bf16_value(O.bf16_bits(w)) for w in Ws]
+    emb64 = O.bf16_value(O.bf16_bits(synth.embedding_host(1000, 512)))
+    ref = O.transformer_logits_f64(plain, W64, emb64, sb[0][:-1])
+    assert O.relative_error(lb[0][0], ref[29]) <= 1e-2
+    assert a.cm.device_status() == 0 and b.cm.device_status() == 0
+    a.close()
+    b.close()
