@@ -387,6 +387,45 @@ def stack_decode_f64(model, W64, h0, eps=1e-5):
     return h
 
 
+# ------------------------------------------------------------------ MoE FFN
+
+def moe_route_f64(z, top_k):
+    """Routing of the MoE model (§5, Qwen3-30B-A3B): per token the top_k
+    experts by router logit (equal logits: the lower expert id first) and
+    their weights, the softmax probabilities of the selected experts
+    renormalised to sum to one. z: [M, E] logits (any precision; the choice
+    is made on these values). Returns (selection [M, k], weights [M, k] FP64)."""
+    z = np.asarray(z)
+    M, E = z.shape
+    sel = np.zeros((M, top_k), np.int64)
+    w = np.zeros((M, top_k), np.float64)
+    for m in range(M):
+        order = sorted(range(E), key=lambda e: (-float(z[m, e]), e))
+        sel[m] = order[:top_k]
+        zz = np.asarray(z[m], np.float64)
+        p = np.exp(zz - zz.max())
+        p /= p.sum()
+        w[m] = p[sel[m]] / p[sel[m]].sum()
+    return sel, w
+
+
+def moe_ffn_f64(x64, Wr64, experts64, top_k, select_logits=None):
+    """MoE FFN in FP64 on logical weights: router logits z = x Wr^T, the
+    routing of moe_route_f64 (decided on `select_logits` when given, e.g.
+    the kernel's FP32 logits), and y = sum_j w_j down_j(silu(gate_j x) *
+    up_j x). experts64[e] = (gate, up, down). Returns (y, z, sel, w)."""
+    x = np.asarray(x64, np.float64)
+    z = linear_f64(x, Wr64)
+    sel, w = moe_route_f64(z if select_logits is None else select_logits, top_k)
+    y = np.zeros((x.shape[0], experts64[0][2].shape[0]))
+    for m in range(x.shape[0]):
+        for j in range(top_k):
+            g, u, d = experts64[sel[m, j]]
+            h = silu(g @ x[m]) * (u @ x[m])
+            y[m] += w[m, j] * (d @ h)
+    return y, z, sel, w
+
+
 # ------------------------------------------------------------- full forward
 
 def rope_f64(x, pos, theta=10000.0):

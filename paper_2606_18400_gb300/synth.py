@@ -26,7 +26,8 @@ DTYPE_SIZE = {DT_F32: 4, DT_BF16: 2, DT_E4M3: 1}
 DTYPE_NAME = {DT_F32: "f32", DT_BF16: "bf16", DT_E4M3: "e4m3"}
 
 # tensor kinds (informational; the layer-stack launch uses them to wire stages)
-K_W1, K_W2, K_Q, K_K, K_V, K_O, K_GATE, K_UP, K_DOWN, K_LMHEAD, K_EMBED = range(11)
+(K_W1, K_W2, K_Q, K_K, K_V, K_O, K_GATE, K_UP, K_DOWN, K_LMHEAD, K_EMBED, K_ROUTER, K_EGATE, K_EUP,
+ K_EDOWN) = range(15)
 
 
 @dataclass
@@ -136,6 +137,40 @@ def decoder(n_layers: int, d_model: int, n_heads: int, n_kv_heads: int,
             Tensor(d_ff, d_model, l, K_UP, g_ff, 0),
             Tensor(d_model, d_ff, l, K_DOWN, g_ff, 1),
         ]
+    return m
+
+
+def moe_block(n_layers: int = 1, d_model: int = 2048, n_experts: int = 128, top_k: int = 8,
+              d_ff: int = 768, spare_pages: int = 64, page_bytes: int = 2 << 20,
+              name: str = "") -> Model:
+    """MoE FFN blocks (the Qwen3-30B-A3B shape by default: d 2048, 128
+    experts of gated MLP 768, top-8), BF16. Per layer a router [n_experts,
+    d_model] whose rows follow the expert-order permutation group (unit 1:
+    the router's stored output e' scores logical expert perm[e']), and per
+    expert gate, up [d_ff, d_model] and down [d_model, d_ff] with their own
+    hidden-unit group (rows of gate/up, columns of down). The tensors of
+    logical expert e are expert_tensors[layer][e] = (gate, up, down)."""
+    tile = 128
+    m = Model(name=name or f"moe{n_experts}x{d_ff}_d{d_model}_{n_layers}L", dtype=DT_BF16, tile_r=tile,
+              tile_c=tile, page_bytes=page_bytes, spare_pages=spare_pages, d_model=d_model, d_ff=d_ff)
+    m.n_experts, m.top_k = n_experts, top_k
+    m.router_tensors, m.expert_groups, m.expert_tensors = [], [], []
+    for l in range(n_layers):
+        g_e = len(m.groups)
+        m.groups.append(Group(n_experts, 1))
+        m.expert_groups.append(g_e)
+        m.router_tensors.append(len(m.tensors))
+        m.tensors.append(Tensor(n_experts, d_model, l, K_ROUTER, g_e, 0))
+        ets = []
+        for e in range(n_experts):
+            g_h = len(m.groups)
+            m.groups.append(Group(d_ff, 1))
+            t0 = len(m.tensors)
+            m.tensors += [Tensor(d_ff, d_model, l, K_EGATE, g_h, 0),
+                          Tensor(d_ff, d_model, l, K_EUP, g_h, 0),
+                          Tensor(d_model, d_ff, l, K_EDOWN, g_h, 1)]
+            ets.append((t0, t0 + 1, t0 + 2))
+        m.expert_tensors.append(ets)
     return m
 
 
