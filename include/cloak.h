@@ -410,6 +410,39 @@ CLOAK_API cloak_status cloak_tune_clear(cloak_ctx *ctx);
  * keygen. Blocks until the move plan is built, then enqueues the moves and
  * returns. Linear calls must not run concurrently with the moves: order them
  * on the same stream or with events. */
+/* A cloaked MoE FFN block (the paper's MoE model, Qwen3-30B-A3B shape:
+ * Section 5). Every expert matrix is a tensor of the context; the router
+ * [n_experts, d_model] has its rows in the order of a keyed expert-order
+ * permutation group (unit 1, n_units = n_experts): its stored output e'
+ * scores logical expert perm[e'] (expert_group = -1: rows not permuted). */
+typedef struct {
+    int32_t n_experts, top_k;   /* 1 <= top_k <= min(n_experts, 16), n_experts <= 1024 */
+    int32_t d_model, d_ff;      /* multiples of 128                                    */
+    int32_t router;             /* tensor [n_experts, d_model]                         */
+    int32_t expert_group;       /* the router rows' group, or -1                       */
+    const int32_t *expert_tensors;  /* host [n_experts][3]: gate [d_ff, d_model], up
+                                   [d_ff, d_model], down [d_model, d_ff] of logical
+                                   expert e (gate/up rows and down columns in one
+                                   hidden order, e.g. one permutation group)        */
+} cloak_moe_desc;
+
+/* y[M, d_model] (FP32) = the MoE FFN of x[M, d_model] (BF16, 16-byte
+ * aligned), 1 <= M <= 64: router logits z = x Wr^T (cloaked linear, FP32);
+ * per token the top_k experts by logit (equal logits: the lower logical
+ * expert), weights = their softmax probabilities renormalised to sum to 1
+ * (FP32); y = sum_j w_j Wdown_j bf16(silu(Wgate_j x) * (Wup_j x)), FP32
+ * accumulation in a fixed order (deterministic). Expert tiles are gathered
+ * through the gather table like every weight (flags: CLOAK_LINEAR_UNCLOAKED
+ * reads the twin, CLOAK_LINEAR_VMM the virtual view). Optional device
+ * outputs: experts_out [M, top_k] the selected logical experts, logits_out
+ * [M, n_experts] the router logits in logical expert order. BF16 models with
+ * 128x128 tiles only. The first call for a descriptor (and the first after a
+ * keygen) uploads the expert table and synchronises the stream; later calls
+ * are asynchronous and capturable. */
+CLOAK_API cloak_status cloak_moe_ffn(cloak_ctx *ctx, const cloak_moe_desc *desc, const void *x_dev,
+                                     float *y_dev, int32_t M, int32_t flags, int32_t *experts_out,
+                                     float *logits_out, void *stream);
+
 CLOAK_API cloak_status cloak_rekey(cloak_ctx *ctx, uint64_t key, uint32_t new_epoch, void *stream);
 
 /* CLOAK_MODEL_VMM contexts: cloak_keygen, cloak_rekey and the last

@@ -63,6 +63,12 @@ class ServeDesc(C.Structure):
                 ("embed_tensor", C.c_int32)]
 
 
+class MoeDesc(C.Structure):
+    _fields_ = [("n_experts", C.c_int32), ("top_k", C.c_int32), ("d_model", C.c_int32), ("d_ff", C.c_int32),
+                ("router", C.c_int32), ("expert_group", C.c_int32),
+                ("expert_tensors", C.POINTER(C.c_int32))]
+
+
 class TuneResult(C.Structure):
     _fields_ = [("chunk", C.c_int32), ("stages", C.c_int32), ("grid", C.c_int32), ("us", C.c_float),
                 ("default_us", C.c_float), ("candidates", C.c_int32), ("l2_prefetch", C.c_int32)]
@@ -110,6 +116,7 @@ SIGNATURES = [
     ("cloak_device_status", _i32, [_vp]),
     ("cloak_vmm_stats", _i32, [_vp, C.POINTER(_i64)]),
     ("cloak_upload", _i32, [_vp, C.POINTER(_vp), _i32, _vp]),
+    ("cloak_moe_ffn", _i32, [_vp, C.POINTER(MoeDesc), _vp, _vp, _i32, _i32, _vp, _vp, _vp]),
     ("cloak_last_error", C.c_char_p, [_vp]),
     ("cloak_launch_count", _i64, [_vp]),
     ("cloak_version", C.c_char_p, []),
@@ -331,6 +338,12 @@ def cloak_vmm_stats(ctx) -> dict:
     return {"pages_remapped": out[0], "remaps": out[1], "chunks": out[2], "remap_us": out[3]}
 
 
+def cloak_moe_ffn(ctx, desc, x_ptr: int, y_ptr: int, M: int, flags: int = 0, experts_out: int = None,
+                  logits_out: int = None, stream=None):
+    _check("cloak_moe_ffn", load().cloak_moe_ffn(ctx, C.byref(desc), x_ptr, y_ptr, M, flags, experts_out,
+                                                 logits_out, _stream(stream)), ctx)
+
+
 def cloak_upload(ctx, host_ptrs, threads: int = 0, stream=None):
     arr = (C.c_void_p * len(host_ptrs))(*host_ptrs)
     _check("cloak_upload", load().cloak_upload(ctx, arr, threads, _stream(stream)), ctx)
@@ -457,6 +470,28 @@ class CloakModel:
         self._stack_tensors = (C.c_int32 * len(order))(*order)
         return StackDesc(len(layers), self._stack_tensors, m.d_model, m.n_heads, m.n_kv_heads,
                          m.head_dim, m.d_ff, eps)
+
+    def moe_desc(self, layer=0):
+        """Descriptor of MoE FFN block `layer` of a ``synth.moe_block`` model."""
+        m = self.model
+        flat = [t for e in m.expert_tensors[layer] for t in e]
+        arr = (C.c_int32 * len(flat))(*flat)
+        d = MoeDesc(m.n_experts, m.top_k, m.d_model, m.d_ff, m.router_tensors[layer],
+                    m.expert_groups[layer], arr)
+        d._keep = arr
+        return d
+
+    def moe_ffn(self, x, desc=None, layer=0, uncloaked=False, vmm=False, experts_out=None,
+                logits_out=None, stream=None):
+        """MoE FFN of BF16 x [M, d_model] -> FP32 y [M, d_model]."""
+        import torch
+        assert x.dtype == torch.bfloat16 and x.is_cuda and x.is_contiguous()
+        d = desc or self.moe_desc(layer)
+        y = torch.empty((x.shape[0], self.model.d_model), dtype=torch.float32, device=x.device)
+        cloak_moe_ffn(self.ctx, d, x.data_ptr(), y.data_ptr(), x.shape[0], _storage(uncloaked, vmm),
+                      experts_out.data_ptr() if experts_out is not None else None,
+                      logits_out.data_ptr() if logits_out is not None else None, stream)
+        return y
 
     def stack_decode(self, h, uncloaked=False, desc=None, stream=None, vmm=False):
         """One decode step of the whole stack; h: FP32 [M, d_model], in place."""

@@ -164,7 +164,7 @@ static void release(cloak_ctx *c) {
     if (c->flags & CLOAK_MODEL_VMM) vmm_release(c); else F(c->arena);
     F(c->twin); F(c->d_scales); F(c->d_part); F(c->d_rowcnt); F(c->d_xq);
     F(c->d_xs); F(c->d_xstage); F(c->d_ystage); F(c->d_plan); F(c->d_status);
-    F(c->d_stack_ws); F(c->d_serve_ws); F(c->d_slot_old); F(c->rk.d_owner); F(c->d_xqp); F(c->d_xsg); F(c->d_gemm_next);
+    F(c->d_stack_ws); F(c->d_serve_ws); F(c->d_slot_old); F(c->d_moe_ws); F(c->rk.d_owner); F(c->d_xqp); F(c->d_xsg); F(c->d_gemm_next);
     for (auto &h : c->h_upload_stage)
         if (h) cudaFreeHost(h);
     if (c->rk.copied) cudaEventDestroy(c->rk.copied);
@@ -547,6 +547,18 @@ extern "C" cloak_status cloak_serve_step(cloak_ctx *ctx, const cloak_serve_desc 
     if (cloak_status rc = storage_ok(ctx, batch->flags)) return rc;
     CLOAK_CUDA(ctx, cudaSetDevice(ctx->device));
     return serve_step_run(ctx, desc, batch, (cudaStream_t)stream);
+}
+
+extern "C" cloak_status cloak_moe_ffn(cloak_ctx *ctx, const cloak_moe_desc *desc, const void *x_dev,
+                                      float *y_dev, int32_t M, int32_t flags, int32_t *experts_out,
+                                      float *logits_out, void *stream) {
+    if (!ctx || !desc || !x_dev || !y_dev || ((uintptr_t)x_dev & 15) ||
+        (flags & ~(CLOAK_LINEAR_UNCLOAKED | CLOAK_LINEAR_VMM)))
+        return CLOAK_E_INVAL;
+    if (!ctx->keyed) return CLOAK_E_STATE;
+    if (cloak_status rc = storage_ok(ctx, flags)) return rc;
+    CLOAK_CUDA(ctx, cudaSetDevice(ctx->device));
+    return moe_run(ctx, desc, x_dev, y_dev, M, flags, experts_out, logits_out, (cudaStream_t)stream);
 }
 
 extern "C" cloak_status cloak_rekey(cloak_ctx *ctx, uint64_t key, uint32_t new_epoch, void *stream) {

@@ -130,6 +130,9 @@ struct cloak_ctx {
     int stack_l2_pf_force = -1;                // set while the tuner measures the stack kernel
     void *d_serve_ws = nullptr;                // serving-step workspace
     size_t serve_ws_cap = 0;
+    void *d_moe_ws = nullptr;                  // MoE FFN workspace (expert table first)
+    size_t moe_ws_cap = 0;
+    std::vector<uint32_t> moe_tab;             // expert table last uploaded
 
     // autotuner: launch shapes per (dtype, shapes, M bucket, output type)
     std::unordered_map<std::string, cloak::TuneCfg> tune;
@@ -182,6 +185,10 @@ cloak_status rekey_run(cloak_ctx *ctx, uint64_t key, uint32_t new_epoch, cudaStr
 cloak_status tile_rekey_run(cloak_ctx *ctx, uint64_t key, uint32_t new_epoch, cudaStream_t s);
 cloak_status rekey_begin(cloak_ctx *ctx, uint64_t key, uint32_t new_epoch, cudaStream_t side);
 cloak_status rekey_advance(cloak_ctx *ctx, cudaStream_t serve, cudaStream_t side, int32_t *done);
+
+// moe.cu
+cloak_status moe_run(cloak_ctx *ctx, const cloak_moe_desc *d, const void *x, float *y, int M, int flags,
+                     int32_t *experts_out, float *logits_out, cudaStream_t s);
 
 // upload.cu
 cloak_status upload_run(cloak_ctx *ctx, const float *const *w, int threads, cudaStream_t s);
