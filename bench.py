@@ -389,7 +389,69 @@ def bench_extras(cloak, synth, torch, dev, stream, key, steps, tune=True):
     out["vmm_page_remap"] = bench_vmm(cloak, synth, torch, dev, stream, key, timed, graph, layer_run)
     out["keyed_upload_llama7b_layer"] = bench_upload(cloak, synth, torch, dev, key)
     out["tile_rekey_llama7b_32L"] = bench_tile_rekey(cloak, synth, torch, dev, stream, key)
+    out["moe_qwen3_30b_a3b_block"] = bench_moe(cloak, synth, torch, dev, stream, key)
     return out
+
+
+def bench_moe(cloak, synth, torch, dev, stream, key, steps=64):
+    """One MoE FFN block of the Qwen3-30B-A3B shape (128 experts of 768 x
+    2048, top-8; 1.2 GB BF16) at decode batch 1 and 4: each step routes
+    different tokens (64 seeded inputs in turn) and L2 is evicted (by reading) between
+    steps, so the selected experts' tiles come from HBM. Graph-replayed
+    steps, timed each with events on the launching stream. L2 is evicted by
+    reading a 256 MB buffer between steps."""
+    model = synth.moe_block()
+    cm = cloak.CloakModel(model, device=dev, twin=True)
+    cm.keygen(key, 0)
+    for t in range(len(model.tensors)):
+        cm.shuffle(t, synth.weights_device(model, t, seed=3))
+    D, E, F, K = model.d_model, model.n_experts, model.d_ff, model.top_k
+    desc = cm.moe_desc()
+    flush = torch.ones(64 << 20, dtype=torch.int32, device="cuda")  # 256 MB
+    flush_sink = torch.zeros((), dtype=torch.int32, device="cuda")
+    res = {"experts": E, "top_k": K, "d_model": D, "d_ff": F}
+    for M in (1, 4):
+        xs = [torch.from_numpy(synth.activations_host(M, D, seed=900 + i)).cuda().to(torch.bfloat16)
+              for i in range(steps)]
+        xb = xs[0].clone()
+        row = {}
+        for name, unc in (("cloaked", False), ("uncloaked", True)):
+            with torch.cuda.stream(stream):
+                cm.moe_ffn(xb, desc=desc, uncloaked=unc, stream=stream.cuda_stream)  # uploads the table
+            torch.cuda.synchronize()
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=stream):
+                yb = cm.moe_ffn(xb, desc=desc, uncloaked=unc, stream=stream.cuda_stream)
+            ts = []
+            with torch.cuda.stream(stream):
+                for i in range(steps):
+                    xb.copy_(xs[i])
+                    # evict L2 by reading (a written flush leaves dirty lines
+                    # whose write-back would land inside the timed step)
+                    flush_sink.copy_(flush.max())
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    g.replay()
+                    b.record(stream)
+                    ts.append((a, b))
+            torch.cuda.synchronize()
+            us = statistics.median(a.elapsed_time(b) for a, b in ts[3:]) * 1e3
+            del g
+            row[name + "_us"] = round(us, 2)
+        # algorithmic bytes: router, the selected experts (distinct per token),
+        # their gather-table entries, x and y
+        wb = E * D * 2 + M * K * 3 * F * D * 2
+        tiles = (E // 128 or 1) * (D // 128) + M * K * 3 * (F // 128) * (D // 128)
+        byts = wb + 4 * tiles + M * D * 2 + M * D * 4
+        row["bytes_per_step"] = byts
+        row["cloaked_gbs"] = round(byts / (row["cloaked_us"] / 1e6) / 1e9, 1)
+        row["uncloaked_gbs"] = round(byts / (row["uncloaked_us"] / 1e6) / 1e9, 1)
+        res[f"decode_M{M}"] = row
+    assert cm.device_status() == 0
+    cm.close()
+    del flush
+    torch.cuda.empty_cache()
+    return res
 
 
 def bench_tile_rekey(cloak, synth, torch, dev, stream, key):
