@@ -39,7 +39,7 @@ def build(force: bool = False) -> str:
 
 
 class _Tensor(C.Structure):
-    _fields_ = [(f, C.c_int32) for f in ("n", "k", "layer", "kind", "perm_group", "perm_axis")]
+    _fields_ = [(f, C.c_int32) for f in ("n", "k", "layer", "kind", "perm_group", "perm_axis", "perm_group2")]
 
 
 class _Group(C.Structure):
@@ -116,8 +116,8 @@ class OracleModel:
     def __init__(self, model):
         self.model = model
         T, Gn = len(model.tensors), len(model.groups)
-        self._t = (_Tensor * T)(*[_Tensor(t.n, t.k, t.layer, t.kind, t.perm_group, t.perm_axis)
-                                  for t in model.tensors])
+        self._t = (_Tensor * T)(*[_Tensor(t.n, t.k, t.layer, t.kind, t.perm_group, t.perm_axis,
+                                          getattr(t, "perm_group2", -1)) for t in model.tensors])
         self._g = (_Group * max(Gn, 1))(*[_Group(g.n_units, g.unit, g.parent, g.ratio)
                                           for g in model.groups])
         self.c = _Model(T, Gn, self._t, self._g, model.dtype, model.tile_r, model.tile_c,

@@ -34,7 +34,10 @@
 typedef unsigned __int128 u128;
 
 /* ---------------------------------------------------------------- model -- */
-typedef struct { int32_t n, k, layer, kind, perm_group, perm_axis; } orc_tensor;
+/* perm_group permutes axis perm_axis (0 rows, 1 columns); perm_group2 the
+ * other axis (the residual dimension, shared by every matrix that reads or
+ * writes the residual stream), -1 for none */
+typedef struct { int32_t n, k, layer, kind, perm_group, perm_axis, perm_group2; } orc_tensor;
 typedef struct { int32_t n_units, unit, parent, ratio; } orc_group;
 typedef struct {
     int32_t num_tensors, num_groups;
@@ -87,10 +90,17 @@ int orc_geometry(const orc_model *m, int64_t *out)
         const orc_tensor *tt = &m->tensors[t];
         if (tt->n <= 0 || tt->k <= 0 || tt->layer < 0) return ORC_EINVAL;
         if (tt->layer + 1 > L) L = tt->layer + 1;
+        if (tt->perm_axis < 0 || tt->perm_axis > 1) return ORC_EINVAL;
         if (tt->perm_group >= 0) {
             if (tt->perm_group >= m->num_groups) return ORC_EINVAL;
             const orc_group *gr = &m->groups[tt->perm_group];
             int64_t dim = tt->perm_axis == 0 ? tt->n : tt->k;
+            if ((int64_t)gr->n_units * gr->unit != dim) return ORC_EINVAL;
+        }
+        if (tt->perm_group2 >= 0) {
+            if (tt->perm_group2 >= m->num_groups) return ORC_EINVAL;
+            const orc_group *gr = &m->groups[tt->perm_group2];
+            int64_t dim = tt->perm_axis == 0 ? tt->k : tt->n;
             if ((int64_t)gr->n_units * gr->unit != dim) return ORC_EINVAL;
         }
         G += (int64_t)((tt->n + m->tile_r - 1) / m->tile_r) * ((tt->k + m->tile_c - 1) / m->tile_c);
@@ -392,12 +402,16 @@ static void axis_maps(const orc_model *m, const orc_tables *tb, int t, int64_t *
     const orc_tensor *tt = &m->tensors[t];
     for (int64_t r = 0; r < tt->n; r++) rmap[r] = r;
     for (int64_t c = 0; c < tt->k; c++) cmap[c] = c;
-    if (tt->perm_group < 0) return;
-    const orc_group *gr = &m->groups[tt->perm_group];
-    const uint32_t *perm = tb->group_perm + group_offset(m, tt->perm_group);
-    int64_t *mp = tt->perm_axis == 0 ? rmap : cmap;
-    int64_t dim = tt->perm_axis == 0 ? tt->n : tt->k;
-    for (int64_t i = 0; i < dim; i++) mp[i] = (int64_t)perm[i / gr->unit] * gr->unit + i % gr->unit;
+    for (int which = 0; which < 2; which++) {
+        const int g = which == 0 ? tt->perm_group : tt->perm_group2;
+        if (g < 0) continue;
+        const int axis = which == 0 ? tt->perm_axis : 1 - tt->perm_axis;
+        const orc_group *gr = &m->groups[g];
+        const uint32_t *perm = tb->group_perm + group_offset(m, g);
+        int64_t *mp = axis == 0 ? rmap : cmap;
+        int64_t dim = axis == 0 ? tt->n : tt->k;
+        for (int64_t i = 0; i < dim; i++) mp[i] = (int64_t)perm[i / gr->unit] * gr->unit + i % gr->unit;
+    }
 }
 
 static int64_t elem_offset(const orc_model *m, const orc_tables *tb, int t, int64_t r, int64_t c,
