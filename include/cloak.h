@@ -68,14 +68,18 @@ enum {
 enum { CLOAK_F32 = 0, CLOAK_BF16 = 1, CLOAK_E4M3 = 2 };
 
 /* One weight matrix. perm_group >= 0 links it to an intra-layer permutation:
- * perm_axis 0 permutes its rows (a producer), 1 its columns (a consumer). The
- * permuted dimension must equal the group's n_units * unit. */
+ * perm_axis 0 permutes its rows (a producer), 1 its columns (a consumer).
+ * perm_group2 >= 0 permutes the other axis (1 - perm_axis) as well: e.g. one
+ * residual-dimension group shared by the columns of every matrix that reads
+ * the residual stream and the rows of every matrix that writes it. Each
+ * permuted dimension must equal its group's n_units * unit. */
 typedef struct {
     int32_t n, k;            /* rows (out features), columns (in features)  */
     int32_t layer;           /* layer index, 0..L-1                          */
     int32_t kind;            /* free tag (q, k, v, o, gate, up, down, ...)   */
     int32_t perm_group;      /* -1: not permuted                             */
     int32_t perm_axis;       /* 0 rows, 1 columns                            */
+    int32_t perm_group2;     /* group of the other axis, -1: none            */
 } cloak_tensor_desc;
 
 /* A keyed permutation of n_units blocks of `unit` rows/columns. A derived

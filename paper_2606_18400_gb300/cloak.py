@@ -35,7 +35,7 @@ class CloakError(RuntimeError):
 
 
 class TensorDesc(C.Structure):
-    _fields_ = [(f, C.c_int32) for f in ("n", "k", "layer", "kind", "perm_group", "perm_axis")]
+    _fields_ = [(f, C.c_int32) for f in ("n", "k", "layer", "kind", "perm_group", "perm_axis", "perm_group2")]
 
 
 class GroupDesc(C.Structure):
@@ -366,8 +366,8 @@ class CloakModel:
     def __init__(self, model: "synth.Model", device: int = 0, twin: bool = False, vmm: bool = False):
         self.model = model
         T, G = len(model.tensors), len(model.groups)
-        self._t = (TensorDesc * T)(*[TensorDesc(t.n, t.k, t.layer, t.kind, t.perm_group, t.perm_axis)
-                                     for t in model.tensors])
+        self._t = (TensorDesc * T)(*[TensorDesc(t.n, t.k, t.layer, t.kind, t.perm_group, t.perm_axis,
+                                                getattr(t, "perm_group2", -1)) for t in model.tensors])
         self._g = (GroupDesc * max(G, 1))(*[GroupDesc(g.n_units, g.unit, g.parent, g.ratio)
                                             for g in model.groups])
         self.desc = ModelDesc(T, G, self._t, self._g, model.dtype, model.tile_r, model.tile_c,

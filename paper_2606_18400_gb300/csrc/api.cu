@@ -120,6 +120,7 @@ static cloak_status validate(const cloak_model_desc *d, cloak_ctx *c) {
         ti.unit = 0;
         ti.goff = 0;
         ti.layer = td.layer;
+        ti.r_unit = ti.r_goff = ti.c_unit = ti.c_goff = 0;
         if (td.perm_group >= 0) {
             if (td.perm_group >= d->num_groups) return CLOAK_E_INVAL;
             const cloak_group_desc &gr = d->groups[td.perm_group];
@@ -127,6 +128,16 @@ static cloak_status validate(const cloak_model_desc *d, cloak_ctx *c) {
             if ((int64_t)gr.n_units * gr.unit != dim) return CLOAK_E_INVAL;
             ti.unit = gr.unit;
             ti.goff = (int32_t)c->goff[td.perm_group];
+            (td.perm_axis == 0 ? ti.r_unit : ti.c_unit) = gr.unit;
+            (td.perm_axis == 0 ? ti.r_goff : ti.c_goff) = ti.goff;
+        }
+        if (td.perm_group2 >= 0) {
+            if (td.perm_group2 >= d->num_groups) return CLOAK_E_INVAL;
+            const cloak_group_desc &gr = d->groups[td.perm_group2];
+            int64_t dim = td.perm_axis == 0 ? td.k : td.n;
+            if ((int64_t)gr.n_units * gr.unit != dim) return CLOAK_E_INVAL;
+            (td.perm_axis == 0 ? ti.c_unit : ti.r_unit) = gr.unit;
+            (td.perm_axis == 0 ? ti.c_goff : ti.r_goff) = (int32_t)c->goff[td.perm_group2];
         }
         // x rows of the tensor-core kernels are read with 16-byte aligned TMA
         if (d->dtype != CLOAK_F32 && (int64_t)td.k * es % 16) return CLOAK_E_UNSUPPORTED;

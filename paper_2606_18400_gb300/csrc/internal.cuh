@@ -22,6 +22,8 @@ struct TensorInfo {
     int32_t perm_group, perm_axis;
     int32_t unit;                // rows/cols per permutation unit (0: none)
     int32_t goff;                // offset of the group permutation in group_perm
+    int32_t r_unit, r_goff;      // the row map's group (unit 0: rows not permuted)
+    int32_t c_unit, c_goff;      // the column map's group (unit 0: columns not permuted)
     int64_t scale_off;           // offset of the tensor's FP8 scales
     int32_t row_off;             // offset of the tensor's tile rows (counters)
     int32_t layer;

@@ -29,10 +29,19 @@ __device__ __forceinline__ int64_t perm_map(const uint32_t *gp, int32_t unit, in
     return (int64_t)gp[i / unit] * unit + i % unit;
 }
 
+// stored row / column -> logical row / column (gp: all group permutations)
+__device__ __forceinline__ int64_t row_map(const uint32_t *gp, const TensorInfo &ti, int64_t r) {
+    return ti.r_unit ? perm_map(gp + ti.r_goff, ti.r_unit, r) : r;
+}
+__device__ __forceinline__ int64_t col_map(const uint32_t *gp, const TensorInfo &ti, int64_t c) {
+    return ti.c_unit ? perm_map(gp + ti.c_goff, ti.c_unit, c) : c;
+}
+
 // per stored row: scale = amax(|row|) / 448 (1 if the row is zero), FP32
+// (the row's column order does not change its maximum)
 __global__ void k_row_scales(const float *W, TensorInfo ti, const uint32_t *gp, float *scales) {
     int64_t r = blockIdx.x;
-    int64_t lr = (ti.perm_group >= 0 && ti.perm_axis == 0) ? perm_map(gp, ti.unit, r) : r;
+    int64_t lr = row_map(gp, ti, r);
     const float *row = W + lr * ti.k;
     float m = 0.0f;
     for (int c = threadIdx.x; c < ti.k; c += blockDim.x) m = fmaxf(m, fabsf(row[c]));
@@ -79,16 +88,14 @@ __global__ void k_shuffle(const float *W, TensorInfo ti, int tile_r, int tile_c,
     const uint32_t g = base + (uint32_t)u;
     T *dst = reinterpret_cast<T *>(arena + (int64_t)slot_of[g] * tile_bytes);
     T *dst2 = twin ? reinterpret_cast<T *>(twin + (int64_t)g * tile_bytes) : nullptr;
-    const bool prow = ti.perm_group >= 0 && ti.perm_axis == 0;
-    const bool pcol = ti.perm_group >= 0 && ti.perm_axis == 1;
     const int elems = tile_r * tile_c;
     for (int e = threadIdx.x; e < elems; e += blockDim.x) {
         int i = e / tile_c, j = e % tile_c;
         int64_t r = nt * tile_r + i, c = kt * tile_c + j;
         float v = 0.0f, s = 1.0f;
         if (r < ti.n && c < ti.k) {
-            int64_t lr = prow ? perm_map(gp, ti.unit, r) : r;
-            int64_t lc = pcol ? perm_map(gp, ti.unit, c) : c;
+            int64_t lr = row_map(gp, ti, r);
+            int64_t lc = col_map(gp, ti, c);
             v = W[lr * ti.k + lc];
             if (ES == 1) s = scales[r];
         }
@@ -109,22 +116,20 @@ __global__ void k_unshuffle(const uint8_t *arena, TensorInfo ti, int tile_r, int
     const int64_t slot = from_twin ? (int64_t)g : (int64_t)slot_of[g];
     const T *src = reinterpret_cast<const T *>(arena + slot * tile_bytes);
     T *o = reinterpret_cast<T *>(out);
-    const bool prow = ti.perm_group >= 0 && ti.perm_axis == 0;
-    const bool pcol = ti.perm_group >= 0 && ti.perm_axis == 1;
     const int elems = tile_r * tile_c;
     for (int e = threadIdx.x; e < elems; e += blockDim.x) {
         int i = e / tile_c, j = e % tile_c;
         int64_t r = nt * tile_r + i, c = kt * tile_c + j;
         if (r >= ti.n || c >= ti.k) continue;
-        int64_t lr = prow ? perm_map(gp, ti.unit, r) : r;
-        int64_t lc = pcol ? perm_map(gp, ti.unit, c) : c;
+        int64_t lr = row_map(gp, ti, r);
+        int64_t lc = col_map(gp, ti, c);
         o[lr * ti.k + lc] = src[e];
     }
 }
 
 cloak_status launch_shuffle(cloak_ctx *ctx, int t, const float *src, cudaStream_t s) {
     const TensorInfo &ti = ctx->info[t];
-    const uint32_t *gp = ti.perm_group >= 0 ? ctx->d_group_perm + ti.goff : nullptr;
+    const uint32_t *gp = ctx->d_group_perm;
     float *sc = ctx->d_scales + ti.scale_off;
     unsigned tiles = (unsigned)(ti.nt * ti.kt);
     uint32_t base = ctx->h_tensor_base[t];
@@ -148,7 +153,7 @@ cloak_status launch_unshuffle(const cloak_ctx *cctx, int t, void *dst, int from_
                               cudaStream_t s) {
     cloak_ctx *ctx = const_cast<cloak_ctx *>(cctx);
     const TensorInfo &ti = ctx->info[t];
-    const uint32_t *gp = ti.perm_group >= 0 ? ctx->d_group_perm + ti.goff : nullptr;
+    const uint32_t *gp = ctx->d_group_perm;
     unsigned tiles = (unsigned)(ti.nt * ti.kt);
     const uint8_t *a = from_twin ? ctx->twin : ctx->arena;
 #define UNSHUF(ES)                                                                          \

@@ -49,6 +49,13 @@ struct HostTables {
 inline int64_t perm_map_h(const uint32_t *gp, int32_t unit, int64_t i) {
     return (int64_t)gp[i / unit] * unit + i % unit;
 }
+// stored row / column -> logical (gp: all group permutations)
+inline int64_t row_map_h(const uint32_t *gp, const TensorInfo &ti, int64_t r) {
+    return ti.r_unit ? perm_map_h(gp + ti.r_goff, ti.r_unit, r) : r;
+}
+inline int64_t col_map_h(const uint32_t *gp, const TensorInfo &ti, int64_t c) {
+    return ti.c_unit ? perm_map_h(gp + ti.c_goff, ti.c_unit, c) : c;
+}
 
 // FP32 -> BF16, round half to even, for a row of n values. For a non-NaN x
 // the 16 discarded bits d of its pattern round the kept half k up exactly
@@ -82,11 +89,10 @@ void row_scales(const cloak_ctx *ctx, const HostTables &h, const float *const *w
         for (size_t j; (j = next.fetch_add(1)) < jobs.size();) {
             const int t = jobs[j].first;
             const TensorInfo &ti = ctx->info[t];
-            const uint32_t *gp = ti.perm_group >= 0 ? h.group_perm.data() + ti.goff : nullptr;
-            const bool prow = ti.perm_group >= 0 && ti.perm_axis == 0;
+            const uint32_t *gp = h.group_perm.data();
             const int64_t r1 = std::min<int64_t>(ti.n, jobs[j].second + 64);
             for (int64_t r = jobs[j].second; r < r1; ++r) {
-                const int64_t lr = prow ? perm_map_h(gp, ti.unit, r) : r;
+                const int64_t lr = row_map_h(gp, ti, r);
                 const float *row = w[t] + lr * ti.k;
                 float m = 0.0f;
                 for (int64_t c = 0; c < ti.k; ++c) m = std::fmax(m, std::fabs(row[c]));
@@ -107,9 +113,8 @@ template <int ES>
 void fill_row_block(const cloak_ctx *ctx, const HostTables &h, const float *const *w, const float *sc,
                     int t, int64_t nt, uint8_t *tiles, float *buf) {
     const TensorInfo &ti = ctx->info[t];
-    const uint32_t *gp = ti.perm_group >= 0 ? h.group_perm.data() + ti.goff : nullptr;
-    const bool prow = ti.perm_group >= 0 && ti.perm_axis == 0;
-    const bool pcol = ti.perm_group >= 0 && ti.perm_axis == 1;
+    const uint32_t *gp = h.group_perm.data();
+    const uint32_t *cgp = gp + ti.c_goff;  // the column map's group
     const int TR = ctx->tile_r, TC = ctx->tile_c;
     const int64_t KP = ti.kt * (int64_t)TC;  // row length padded to whole tiles
     uint8_t *blk = tiles + ((int64_t)ctx->h_tensor_base[t] + nt * ti.kt) * ctx->tile_bytes;
@@ -120,17 +125,17 @@ void fill_row_block(const cloak_ctx *ctx, const HostTables &h, const float *cons
                 std::memset(blk + kt * ctx->tile_bytes + (size_t)i * TC * ES, 0, (size_t)TC * ES);
             continue;
         }
-        const float *row = w[t] + (prow ? perm_map_h(gp, ti.unit, r) : r) * ti.k;
+        const float *row = w[t] + row_map_h(gp, ti, r) * ti.k;
         // the stored row, zero-padded to whole tiles: read in place when its
         // columns keep their order (only a ragged last tile goes through buf)
         const float *src = buf;
-        if (!pcol) {
+        if (!ti.c_unit) {
             if (KP == ti.k) src = row;
             else std::memcpy(buf, row, (size_t)ti.k * 4);
-        } else if (ti.unit == 1) {
-            for (int64_t c = 0; c < ti.k; ++c) buf[c] = row[gp[c]];
+        } else if (ti.c_unit == 1) {
+            for (int64_t c = 0; c < ti.k; ++c) buf[c] = row[cgp[c]];
         } else {
-            for (int64_t c = 0; c < ti.k; ++c) buf[c] = row[perm_map_h(gp, ti.unit, c)];
+            for (int64_t c = 0; c < ti.k; ++c) buf[c] = row[perm_map_h(cgp, ti.c_unit, c)];
         }
         if (src == buf)
             for (int64_t c = ti.k; c < KP; ++c) buf[c] = 0.0f;

@@ -48,7 +48,7 @@ def test_version(lib):
 
 def _desc(cloak, **kw):
     t = (cloak.TensorDesc * 1)(cloak.TensorDesc(kw.get("n", 256), kw.get("k", 256), 0, 0,
-                                                kw.get("pg", -1), kw.get("axis", 0)))
+                                                kw.get("pg", -1), kw.get("axis", 0), kw.get("pg2", -1)))
     g = (cloak.GroupDesc * 1)(cloak.GroupDesc(kw.get("units", 256), 1, -1, 1))
     d = cloak.ModelDesc(1, kw.get("ngroups", 0), t, g, kw.get("dtype", 1), kw.get("tr", 128),
                         kw.get("tc", 128), 0, kw.get("scope", 0), 0, kw.get("page", 2 << 20))
@@ -61,6 +61,9 @@ def _desc(cloak, **kw):
     (dict(tr=64, tc=64), -6),                 # BF16 needs 128x128 tiles
     (dict(pg=0, ngroups=1, units=100), -1),   # permuted dim != units * unit
     (dict(pg=3, ngroups=1), -1),              # group out of range
+    (dict(pg2=0, ngroups=1, units=100), -1),  # second axis != units * unit
+    (dict(pg2=2, ngroups=1), -1),             # second group out of range
+    (dict(axis=2), -1),                       # no such axis
     (dict(scope=2), -1),
     (dict(n=0), -1),
 ])
