@@ -882,7 +882,9 @@ def run_profile(args):
     fp8    -- one GQA E4M3 layer (233 MB), grouped decode M=1, 3 launches;
     fp8prefill -- the same layer, grouped prefill M=2048 (the prefill GEMM), 3 launches;
     prefill-- one 7B-class layer, grouped M=2048 (the prefill GEMM), 3 launches;
-    decode -- one 7B-class layer, grouped M=1 (the headline step), 3 launches.
+    decode -- one 7B-class layer, grouped M=1 (the headline step), 3 launches;
+    moe    -- one MoE block of the Qwen3-30B-A3B shape (1.2 GB), decode M=1,
+              3 steps (4 kernels each), a different token per step.
     The linears' launch shape is tuned first (unless --no-tune); the profiled
     launches sit inside the NVTX range "profiled" (ncu --nvtx
     --nvtx-include "profiled/")."""
@@ -892,6 +894,8 @@ def run_profile(args):
     torch.cuda.set_device(0)
     if args.profile == "stack":
         model = synth.llama7b_layer(4)
+    elif args.profile == "moe":
+        model = synth.moe_block()
     elif args.profile in ("fp8", "fp8prefill"):
         model = synth.gqa28_fp8(1)
     else:
@@ -901,7 +905,18 @@ def run_profile(args):
     for t in range(len(model.tensors)):
         cm.shuffle(t, synth.weights_device(model, t, seed=0))
     torch.cuda.synchronize()
-    if args.profile == "stack":
+    if args.profile == "moe":
+        xs = [torch.from_numpy(synth.activations_host(1, model.d_model, seed=900 + i)).cuda().to(torch.bfloat16)
+              for i in range(4)]
+        desc = cm.moe_desc()
+        cm.moe_ffn(xs[3], desc=desc)  # uploads the expert table
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("profiled")
+        for i in range(3):
+            cm.moe_ffn(xs[i], desc=desc)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+    elif args.profile == "stack":
         h0 = torch.from_numpy(synth.activations_host(1, 4096, seed=1)).cuda()
         torch.cuda.nvtx.range_push("profiled")
         for _ in range(3):
@@ -938,7 +953,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--serve", action="store_true", help="run the serving sweep instead")
-    ap.add_argument("--profile", choices=["stack", "fp8", "fp8prefill", "prefill", "decode"],
+    ap.add_argument("--profile", choices=["stack", "fp8", "fp8prefill", "prefill", "decode", "moe"],
                     help="small case for ncu")
     ap.add_argument("--rates", default="2,8,32")
     ap.add_argument("--serve-seconds", type=float, default=30.0)
