@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <exception>
 #include <mutex>
 
 #include "internal.cuh"
@@ -377,7 +378,13 @@ extern "C" cloak_status cloak_upload(cloak_ctx *ctx, const float *const *w_host,
         if (!w_host[t]) return CLOAK_E_INVAL;
     if (!ctx->keyed || ctx->rk.active || ctx->twin) return CLOAK_E_STATE;
     CLOAK_CUDA(ctx, cudaSetDevice(ctx->device));
-    return upload_run(ctx, w_host, threads, (cudaStream_t)stream);
+    // host threads and buffers: no C++ exception may cross the C boundary
+    try {
+        return upload_run(ctx, w_host, threads, (cudaStream_t)stream);
+    } catch (const std::exception &e) {
+        ctx->last_err = std::string("keyed upload: ") + e.what();
+        return CLOAK_E_NOMEM;
+    }
 }
 
 extern "C" cloak_status cloak_vmm_stats(const cloak_ctx *ctx, int64_t out[4]) {
