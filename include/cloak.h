@@ -491,6 +491,15 @@ CLOAK_API cloak_status cloak_rekey_advance(cloak_ctx *ctx, void *serve_stream, v
  * last call; reading it synchronises the device and clears it. */
 CLOAK_API cloak_status cloak_device_status(cloak_ctx *ctx);
 
+/* Failure-detection self-test, with no fault: one block runs two waits that
+ * nothing satisfies -- the bounded mbarrier wait every pipelined kernel uses,
+ * on a barrier nothing arrives at, and a bounded spin on a device flag
+ * nothing sets. Each must give up after its limit (2 s) and record
+ * CLOAK_E_TIMEOUT in the status word cloak_device_status reads. Blocks about
+ * 2 s; clears the status afterwards; the context stays usable. CLOAK_OK when
+ * both waits reported their timeout, CLOAK_E_CUDA (with a message) if not. */
+CLOAK_API cloak_status cloak_check_waits(cloak_ctx *ctx, void *stream);
+
 /* Text of the last CUDA error recorded in this context (or ""). */
 CLOAK_API const char *cloak_last_error(const cloak_ctx *ctx);
 

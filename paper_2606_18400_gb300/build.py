@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libcloak.so")
-SOURCES = ["api.cu", "keygen.cu", "layout.cu", "rekey.cu", "linear.cu", "gemm.cu", "noalloc.cu", "vmm.cu", "upload.cu", "moe.cu", "stack.cu", "serve.cu", "tune.cu"]
+SOURCES = ["api.cu", "keygen.cu", "layout.cu", "rekey.cu", "linear.cu", "gemm.cu", "noalloc.cu", "vmm.cu", "upload.cu", "moe.cu", "selftest.cu", "stack.cu", "serve.cu", "tune.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "-I", os.path.join(ROOT, "include")]

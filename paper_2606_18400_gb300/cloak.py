@@ -114,6 +114,7 @@ SIGNATURES = [
     ("cloak_tune_clear", _i32, [_vp]),
     ("cloak_rekey_advance", _i32, [_vp, _vp, _vp, C.POINTER(_i32)]),
     ("cloak_device_status", _i32, [_vp]),
+    ("cloak_check_waits", _i32, [_vp, _vp]),
     ("cloak_vmm_stats", _i32, [_vp, C.POINTER(_i64)]),
     ("cloak_upload", _i32, [_vp, C.POINTER(_vp), _i32, _vp]),
     ("cloak_moe_ffn", _i32, [_vp, C.POINTER(MoeDesc), _vp, _vp, _i32, _i32, _vp, _vp, _vp]),
@@ -338,6 +339,10 @@ def cloak_vmm_stats(ctx) -> dict:
     return {"pages_remapped": out[0], "remaps": out[1], "chunks": out[2], "remap_us": out[3]}
 
 
+def cloak_check_waits(ctx, stream=None):
+    _check("cloak_check_waits", load().cloak_check_waits(ctx, _stream(stream)), ctx)
+
+
 def cloak_moe_ffn(ctx, desc, x_ptr: int, y_ptr: int, M: int, flags: int = 0, experts_out: int = None,
                   logits_out: int = None, stream=None):
     _check("cloak_moe_ffn", load().cloak_moe_ffn(ctx, C.byref(desc), x_ptr, y_ptr, M, flags, experts_out,
@@ -544,6 +549,10 @@ class CloakModel:
 
     def device_status(self):
         return cloak_device_status(self.ctx)
+
+    def check_waits(self, stream=None):
+        """Run the bounded-wait self-test (raises if a wait did not time out)."""
+        cloak_check_waits(self.ctx, stream)
 
     def vmm_stats(self) -> dict:
         return cloak_vmm_stats(self.ctx)

@@ -666,6 +666,12 @@ extern "C" cloak_status cloak_device_status(cloak_ctx *ctx) {
     return st;
 }
 
+extern "C" cloak_status cloak_check_waits(cloak_ctx *ctx, void *stream) {
+    if (!ctx) return CLOAK_E_INVAL;
+    CLOAK_CUDA(ctx, cudaSetDevice(ctx->device));
+    return check_waits_run(ctx, (cudaStream_t)stream);
+}
+
 extern "C" const char *cloak_last_error(const cloak_ctx *ctx) {
     return ctx ? ctx->last_err.c_str() : "";
 }

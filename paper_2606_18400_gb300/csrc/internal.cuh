@@ -188,6 +188,9 @@ cloak_status tile_rekey_run(cloak_ctx *ctx, uint64_t key, uint32_t new_epoch, cu
 cloak_status rekey_begin(cloak_ctx *ctx, uint64_t key, uint32_t new_epoch, cudaStream_t side);
 cloak_status rekey_advance(cloak_ctx *ctx, cudaStream_t serve, cudaStream_t side, int32_t *done);
 
+// selftest.cu
+cloak_status check_waits_run(cloak_ctx *ctx, cudaStream_t s);
+
 // moe.cu
 cloak_status moe_run(cloak_ctx *ctx, const cloak_moe_desc *d, const void *x, float *y, int M, int flags,
                      int32_t *experts_out, float *logits_out, cudaStream_t s);
