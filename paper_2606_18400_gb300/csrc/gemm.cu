@@ -290,10 +290,10 @@ template <bool FP8>
 static cloak_status gemm_launch(cloak_ctx *ctx, const CUtensorMap &tw, const GemmMaps &mp, const GemmArgs &g,
                                 int grid, cudaStream_t s) {
     using C = GemmCfg<FP8>;
-    static bool attr_set = false;  // per instantiation; once per process
-    if (!attr_set) {
+    static std::atomic<uint64_t> attr_devs{0};  // per instantiation: devices set up
+    if (attr_needed(attr_devs, ctx->device)) {
         CLOAK_CUDA(ctx, cudaFuncSetAttribute(k_gemm_tc<FP8>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
-        attr_set = true;
+        attr_set_on(attr_devs, ctx->device);
     }
     k_gemm_tc<FP8><<<grid, 192, C::SMEM, s>>>(tw, mp, g);
     CLOAK_LAUNCHED(ctx);

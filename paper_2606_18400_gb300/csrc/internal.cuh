@@ -4,6 +4,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <string>
 #include <unordered_map>
@@ -14,6 +15,16 @@
 namespace cloak {
 
 constexpr uint32_t NONE = 0xFFFFFFFFu;
+
+// A kernel attribute set with cudaFuncSetAttribute holds for one device:
+// `done` records the devices (below 64) it has been set on. Setting it again
+// is harmless, so two threads racing here both just set it.
+inline bool attr_needed(const std::atomic<uint64_t> &done, int device) {
+    return device < 0 || device >= 64 || !(done.load(std::memory_order_relaxed) & (1ull << device));
+}
+inline void attr_set_on(std::atomic<uint64_t> &done, int device) {
+    if (device >= 0 && device < 64) done.fetch_or(1ull << device, std::memory_order_relaxed);
+}
 constexpr uint64_t SM64_GAMMA = 0x9E3779B97F4A7C15ull;
 
 // per-tensor geometry uploaded to the device

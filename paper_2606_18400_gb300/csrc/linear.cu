@@ -625,11 +625,11 @@ template <bool FP8, int NPAD>
 static cloak_status launch_tc(cloak_ctx *ctx, const CUtensorMap &tw, const void *const *xs,
                               TcBatch &b, const TuneCfg &cfg, cudaStream_t s) {
     using C = TcCfg<FP8, NPAD>;
-    static bool attr_set = false;  // per instantiation; once per process
-    if (!attr_set) {
+    static std::atomic<uint64_t> attr_devs{0};  // per instantiation: devices set up
+    if (attr_needed(attr_devs, ctx->device)) {
         CLOAK_CUDA(ctx, cudaFuncSetAttribute(k_linear_tc<FP8, NPAD>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
-        attr_set = true;
+        attr_set_on(attr_devs, ctx->device);
     }
     TxMaps tx;
     const int es = FP8 ? 1 : 2;

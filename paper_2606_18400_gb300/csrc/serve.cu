@@ -586,11 +586,11 @@ static cloak_status serve_step_body(cloak_ctx *ctx, const cloak_serve_desc *d,
     float *apart = (float *)take(part_bytes);
     cloak_status rc;
     if (b->qtiles) {
-        static bool attr = false;
-        if (!attr) {
+        static std::atomic<uint64_t> attr_devs{0};  // devices set up
+        if (attr_needed(attr_devs, ctx->device)) {
             CLOAK_CUDA(ctx, cudaFuncSetAttribute(k_attention_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  4 * ATT_TILE_BYTES));
-            attr = true;
+            attr_set_on(attr_devs, ctx->device);
         }
     }
     if (d->embed_tensor >= 0) {
