@@ -610,9 +610,12 @@ cloak_status tile_rekey_run(cloak_ctx *ctx, uint64_t key, uint32_t new_epoch, cu
     if (!in_place && cudaMallocAsync((void **)&tmp, bytes, s) == cudaSuccess) {
         k_tile_gather<<<ctx->sm_count * 8, 256, 0, s>>>(ctx->d_slot_old, ctx->d_tile_slot, (uint32_t)ctx->G,
                                                         ctx->arena, tmp, ctx->tile_bytes);
-        CLOAK_LAUNCHED(ctx);
-        CLOAK_CUDA(ctx, cudaMemcpyAsync(ctx->arena, tmp, bytes, cudaMemcpyDeviceToDevice, s));
-        CLOAK_CUDA(ctx, cudaFreeAsync(tmp, s));
+        ctx->launches++;
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->arena, tmp, bytes, cudaMemcpyDeviceToDevice, s);
+        const cudaError_t ef = cudaFreeAsync(tmp, s);  // released on every path
+        if (e == cudaSuccess) e = ef;
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "tile re-key (out of place)");
     } else {
         if (!in_place) cudaGetLastError();  // the failed allocation is not a sticky error
         const MoveSet m{ctx->d_slot_old, ctx->d_tile_slot, (uint32_t)ctx->G, (uint32_t)(ctx->NPS * ctx->tpp),
