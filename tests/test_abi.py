@@ -101,7 +101,7 @@ def test_struct_layouts_match_the_header(tmp_path):
     structs = {"cloak_tensor_desc": cloak.TensorDesc, "cloak_group_desc": cloak.GroupDesc,
                "cloak_model_desc": cloak.ModelDesc, "cloak_stack_desc": cloak.StackDesc,
                "cloak_serve_desc": cloak.ServeDesc, "cloak_serve_batch": cloak.ServeBatch,
-               "cloak_tune_result": cloak.TuneResult}
+               "cloak_tune_result": cloak.TuneResult, "cloak_moe_desc": cloak.MoeDesc}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "cloak.h"', 'int main(void) {']
     for cname, py in structs.items():
         lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
