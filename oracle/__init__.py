@@ -10,7 +10,20 @@ Layout (tables, shuffle, unshuffle, re-key, number formats) is plain C in
 matrix products on the logical, unshuffled weights: the method leaves the
 function a network computes unchanged (Abstract: authorised execution sees a
 valid view), so the reference result of a cloaked linear, MLP or layer is the
-textbook product on the logical weights.
+textbook product on the logical weights. The MoE FFN (the paper's MoE model,
+Section 5) is written out the same way: softmax top-k routing over the
+router's logits, renormalised weights, the selected experts' gated MLPs.
+
+Pins (tests/test_oracle_*.py): the PRNG's published known answers, the
+bounded draw's exact arithmetic, tables being permutations meeting the
+layout invariants, shuffle/unshuffle round trips and independent NumPy
+restatements of the stored matrices (one or two permuted axes), fresh
+shuffles equal to re-keys (pages or tiles), compensated networks computing
+the plain network's function (brute force on integer MLPs, a GQA layer, the
+stack and full model under the residual permutation), the BF16/E4M3 codecs
+against their format definitions, and the MoE routing's closed forms
+(identical experts, top-1, the all-experts softmax mixture, relabelling,
+ties).
 """
 from __future__ import annotations
 
