@@ -135,7 +135,12 @@ typedef struct cloak_ctx cloak_ctx;
 
 /* Create a context on `device`: validates the descriptor, allocates the
  * zeroed arena of (ceil(tiles / tiles_per_page) + spare_pages) pages, the twin
- * if requested, tables and workspaces. Synchronous. */
+ * if requested, tables and workspaces. Synchronous. Paper: Section 4.2
+ * ("Physical page remapping", Table 1b) places weights on non-contiguous
+ * physical pages of a fixed size; the arena is that page pool, allocated
+ * whole before anything is placed (Section 5, "Implementation Details"). The
+ * context owns every buffer it allocates; errors: CLOAK_E_INVAL (descriptor),
+ * CLOAK_E_NOMEM, CLOAK_E_CUDA. */
 CLOAK_API cloak_status cloak_create(const cloak_model_desc *desc, int32_t device, cloak_ctx **out);
 
 /* Release everything the context owns. Synchronises the device first. */
@@ -170,12 +175,24 @@ CLOAK_API cloak_status cloak_export_table(const cloak_ctx *ctx, int32_t which, u
  * permute rows or columns, convert to the storage type (BF16: round to
  * nearest even; E4M3: per-stored-row scale amax/448 then round to nearest
  * even, saturating), cut into tiles, write each tile to its keyed slot, and to
- * the twin if present. Ragged tile edges are written as zeros. */
+ * the twin if present. Ragged tile edges are written as zeros. Paper: the
+ * keyed placement of Section 5 ("Implementation Details": permutation before
+ * any weight is placed) combining inter- and intra-layer weight shuffling
+ * (Abstract; Contributions) with the page placement of Section 4.2. The caller
+ * keeps ownership of logical_dev (read only, asynchronous on `stream`: keep it
+ * alive until the stream reaches this point). Errors: CLOAK_E_INVAL (tensor
+ * index, null pointer), CLOAK_E_STATE before a keygen or during a concurrent
+ * re-key. */
 CLOAK_API cloak_status cloak_shuffle(cloak_ctx *ctx, int32_t tensor, const float *logical_dev, void *stream);
 
 /* Inverse of cloak_shuffle: read the tiles back and write the logical
  * [n, k] matrix in the storage type (FP32 values, BF16 or E4M3 bit patterns)
- * with the permutation undone. from_twin = 1 reads the uncloaked twin. */
+ * with the permutation undone. from_twin = 1 reads the uncloaked twin. Paper:
+ * the authorised execution keeps a valid logical view of the weights
+ * (Abstract; Section 4.2, pointers and access semantics unchanged); this is
+ * that view materialised. logical_dev is caller-owned, [n, k] elements of the
+ * storage type, row-major. Errors: CLOAK_E_INVAL, CLOAK_E_STATE (not keyed,
+ * no twin for from_twin = 1). */
 CLOAK_API cloak_status cloak_unshuffle(const cloak_ctx *ctx, int32_t tensor, void *logical_dev,
                              int32_t from_twin, void *stream);
 
@@ -230,7 +247,13 @@ enum { CLOAK_OUT_F32 = 0, CLOAK_OUT_BF16 = 1 };
  * models and BF16 otherwise (E4M3 models quantise x per row inside the call:
  * scale amax/448, round to nearest even). Accumulation is FP32; with the same
  * M, the cloaked and uncloaked kernels sum in the same order and agree bit for
- * bit. x and y must not alias; x must be 16-byte aligned. 1 <= M <= 65536. */
+ * bit. x and y must not alias; x must be 16-byte aligned. 1 <= M <= 65536.
+ * Paper: the authorised execution's valid logical view (Abstract; Section 4.2:
+ * the engine computes on the weights as if they were contiguous, with no
+ * measurable overhead, Figure 5). x [M, k] and y [M, n] are row-major,
+ * caller-owned device buffers; asynchronous on `stream`; workspaces are
+ * context-owned and may grow (cudaMalloc). Errors: CLOAK_E_INVAL (arguments),
+ * CLOAK_E_STATE (not keyed; uncloaked without a twin), CLOAK_E_CUDA. */
 CLOAK_API cloak_status cloak_linear(cloak_ctx *ctx, int32_t tensor, const void *x_dev, void *y_dev,
                           int32_t M, int32_t out_dtype, int32_t flags, void *stream);
 
@@ -269,18 +292,23 @@ CLOAK_API cloak_status cloak_linear_batch_host(cloak_ctx *ctx, int32_t n, const 
  * real-time paths where cudaMalloc's synchronisation is not allowed.
  * cloak_linear itself may grow its context-owned scratch with cudaMalloc; this
  * call never calls cudaMalloc, cudaFree or any allocating routine. Its scratch
- * (split-K partial sums and tile-row counters) is one fixed 5 MiB + 16 KiB
+ * (split-K partial sums and tile-row counters) is one fixed 20 MiB + 16 KiB
  * device array inside the library, held on every GPU that loads it until the
  * process exits. The paper has no counterpart: this is a deployment aid.
- *   Limits: BF16 models only (else CLOAK_E_UNSUPPORTED); 1 <= M <= 32 and at
- *   most 4096 tile rows per tensor (else CLOAK_E_INVAL, message in
- *   cloak_last_error).
- *   The first call on a device looks up the array's device address and zeroes
- *   its counters (synchronous); make that first call before any stream
- *   capture. Every call shares the one array and clears the counters it uses
- *   on `stream`; calls that overlap on the GPU (other streams, other contexts)
- *   race on it and must be ordered by the caller.
- * Results equal cloak_linear's for the same arguments. */
+ *   Limits: BF16 models only, devices of at most 160 SMs (else
+ *   CLOAK_E_UNSUPPORTED); 1 <= M <= 32 and at most 4096 tile rows per tensor
+ *   (else CLOAK_E_INVAL); a launch shape stored for the tensor (tuner or
+ *   cloak_tune_load) of more than 4 CTAs per SM of a 160-SM device
+ *   (CLOAK_E_UNSUPPORTED). Messages in cloak_last_error.
+ *   The first call on a device looks up the array's device address; make that
+ *   first call before any stream capture. A failed look-up is reported and
+ *   retried by the next call. Every call shares the one array and clears the
+ *   counters it uses on `stream` (an asynchronous memset); calls that overlap
+ *   on the GPU (other streams, other contexts) race on it and must be ordered
+ *   by the caller.
+ * It launches the kernel cloak_linear launches, in the launch shape cloak_linear
+ * takes for the same tensor and M (the stored tuned shape, else the default),
+ * so results equal cloak_linear's for the same arguments, bit for bit. */
 CLOAK_API cloak_status cloak_linear_noalloc(cloak_ctx *ctx, int32_t tensor, const void *x_dev,
                                             void *y_dev, int32_t M, int32_t out_dtype,
                                             int32_t flags, void *stream);
