@@ -258,6 +258,6 @@ cloak_status gemm_run(cloak_ctx *ctx, int n, const int32_t *tensors, const void 
                       const uint32_t *slot_of, const CUtensorMap &tw, cudaStream_t s);
 cloak_status linear_run_given_scratch(cloak_ctx *ctx, int t, const void *x, void *y, int M,
                                       int out_dtype, int flags, float *part, size_t part_floats,
-                                      uint32_t *rowcnt, uint32_t max_grid, cudaStream_t s);
+                                      uint32_t *rowcnt, cudaStream_t s);
 
 }  // namespace cloak

@@ -866,59 +866,82 @@ cloak_status linear_batch_run(cloak_ctx *ctx, int n, const int32_t *tensors, con
 }
 
 // Same BF16 launch with scratch supplied by the caller: nothing is allocated.
+// The launch shape is the one cloak_linear would use for these arguments (the
+// tuned token chunk, ring depth and CTA count, or the defaults), so the split
+// of every tile row, and with it the summation order, is the same.
 // part_floats must hold grid * 2 * 128 * NPAD floats; rowcnt holds one zeroed
 // counter per tile row of the tensor.
 template <int NPAD>
 static cloak_status launch_tc_given(cloak_ctx *ctx, const CUtensorMap &tw, const void *x,
-                                    TcBatch &b, size_t part_floats, uint32_t max_grid,
+                                    TcBatch &b, const TuneCfg &cfg, size_t part_floats,
                                     cudaStream_t s) {
     using C = TcCfg<false, NPAD>;
-    CLOAK_CUDA(ctx, cudaFuncSetAttribute(k_linear_tc<false, NPAD>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+    static std::atomic<uint64_t> attr_devs{0};  // per instantiation: devices set up
+    if (attr_needed(attr_devs, ctx->device)) {
+        CLOAK_CUDA(ctx, cudaFuncSetAttribute(k_linear_tc<false, NPAD>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+        attr_set_on(attr_devs, ctx->device);
+    }
     TxMaps tx;
     if (!encode_tmap_2d(&tx.m[0], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, x, (uint64_t)b.p[0].K,
                         (uint64_t)b.M, (uint64_t)b.p[0].K * 2, 64, NPAD)) {
         ctx->last_err = "cuTensorMapEncodeTiled failed for x";
         return CLOAK_E_CUDA;
     }
-    const uint32_t grid = (uint32_t)std::min<uint64_t>(
-        b.total, std::min<uint64_t>((uint64_t)ctx->sm_count, (uint64_t)max_grid));
-    if ((size_t)grid * 2 * 128 * NPAD > part_floats) return CLOAK_E_INVAL;
-    b.stages = C::STAGES;
-    k_linear_tc<false, NPAD><<<grid, 192, C::SMEM, s>>>(tw, tx, b);
+    b.stages = (cfg.stages >= 1 && cfg.stages <= C::STAGES) ? cfg.stages : C::STAGES;
+    const uint32_t want = cfg.grid > 0 ? (uint32_t)cfg.grid : (uint32_t)ctx->sm_count;
+    const uint32_t grid = (uint32_t)std::min<uint64_t>(b.total, want);
+    if ((size_t)grid * 2 * 128 * NPAD > part_floats) {
+        ctx->last_err = "cloak_linear_noalloc: the stored launch shape needs more CTAs than the fixed scratch holds";
+        return CLOAK_E_UNSUPPORTED;
+    }
+    const size_t smem = (size_t)b.stages * C::STAGE + 1024 + 1024;
+    k_linear_tc<false, NPAD><<<grid, 192, smem, s>>>(tw, tx, b);
     CLOAK_LAUNCHED(ctx);
     return CLOAK_OK;
 }
 
 cloak_status linear_run_given_scratch(cloak_ctx *ctx, int t, const void *x, void *y, int M,
                                       int out_dtype, int flags, float *part, size_t part_floats,
-                                      uint32_t *rowcnt, uint32_t max_grid, cudaStream_t s) {
+                                      uint32_t *rowcnt, cudaStream_t s) {
     if (ctx->dtype != CLOAK_BF16) return CLOAK_E_UNSUPPORTED;
     if (M < 1 || M > 32) return CLOAK_E_INVAL;
     const bool unc = flags & CLOAK_LINEAR_UNCLOAKED;
     const TensorInfo &ti = ctx->info[t];
-    TcBatch b{};
-    b.slot_of = unc ? nullptr : ctx->d_tile_slot;
-    b.np = 1;
-    b.M = M;
-    b.out_f32 = out_dtype == CLOAK_OUT_F32;
-    b.relu = (flags & CLOAK_LINEAR_RELU) ? 1 : 0;
-    b.status = ctx->d_status;
-    b.part = part;
-    TcProblem &P = b.p[0];
-    P.u_begin = 0;
-    P.base = ctx->h_tensor_base[t];
-    P.N = ti.n;
-    P.K = ti.k;
-    P.NT = ti.nt;
-    P.KT = ti.kt;
-    P.UPR = ti.kt;
-    P.y = y;
-    P.rowcnt = rowcnt;
-    b.total = (uint64_t)ti.nt * ti.kt;
+    // the launch shape cloak_linear takes for this batch (linear_batch_run)
+    const int32_t tt[1] = {t};
+    TuneCfg cfg = tune_lookup(ctx, 1, tt, M, out_dtype);
+    if (ctx->tune_invariant) cfg.grid = 0;
+    const int chunk = cfg.chunk > 0 ? cfg.chunk : 256;
+    const int oes = out_dtype == CLOAK_OUT_F32 ? 4 : 2;
     const CUtensorMap &tw = unc ? ctx->tmap_twin : ctx->tmap_arena;
-    if (M <= 16) return launch_tc_given<16>(ctx, tw, x, b, part_floats, max_grid, s);
-    return launch_tc_given<32>(ctx, tw, x, b, part_floats, max_grid, s);
+    for (int m0 = 0; m0 < M; m0 += chunk) {
+        const int mb = std::min(chunk, M - m0);
+        TcBatch b{};
+        b.slot_of = unc ? nullptr : ctx->d_tile_slot;
+        b.np = 1;
+        b.M = mb;
+        b.out_f32 = out_dtype == CLOAK_OUT_F32;
+        b.relu = (flags & CLOAK_LINEAR_RELU) ? 1 : 0;
+        b.status = ctx->d_status;
+        b.part = part;
+        TcProblem &P = b.p[0];
+        P.u_begin = 0;
+        P.base = ctx->h_tensor_base[t];
+        P.N = ti.n;
+        P.K = ti.k;
+        P.NT = ti.nt;
+        P.KT = ti.kt;
+        P.UPR = ti.kt;
+        P.y = (uint8_t *)y + (size_t)m0 * ti.n * oes;
+        P.rowcnt = rowcnt;
+        b.total = (uint64_t)ti.nt * ti.kt;
+        const uint8_t *xm = (const uint8_t *)x + (size_t)m0 * ti.k * 2;
+        const cloak_status rc = mb <= 16 ? launch_tc_given<16>(ctx, tw, xm, b, cfg, part_floats, s)
+                                         : launch_tc_given<32>(ctx, tw, xm, b, cfg, part_floats, s);
+        if (rc) return rc;
+    }
+    return CLOAK_OK;
 }
 
 cloak_status linear_run(cloak_ctx *ctx, int t, const void *x, void *y, int M, int out_dtype,

@@ -12,12 +12,15 @@
 namespace cloak {
 namespace {
 
-// Limits of the allocation-free path.
-constexpr int NOALLOC_MAX_M = 32;           // rows of x (MMA N padded to 16 or 32)
-constexpr uint32_t NOALLOC_MAX_GRID = 160;  // CTAs (one per SM; GB300 has 152)
-constexpr uint32_t NOALLOC_MAX_ROWS = 4096; // tile rows of one tensor (n <= 524,288)
+// Limits of the allocation-free path. The array holds the partial sums of
+// the largest launch cloak_linear can make for these batches: the autotuner
+// tries up to 4 CTAs per SM, and devices of up to 160 SMs are supported.
+constexpr int NOALLOC_MAX_M = 32;                        // rows of x (MMA N padded to 16 or 32)
+constexpr uint32_t NOALLOC_MAX_SMS = 160;                // SMs of the device (GB300: 152)
+constexpr uint32_t NOALLOC_MAX_GRID = 4 * NOALLOC_MAX_SMS;  // CTAs of one launch
+constexpr uint32_t NOALLOC_MAX_ROWS = 4096;              // tile rows of one tensor (n <= 524,288)
 constexpr size_t NOALLOC_PART_FLOATS = (size_t)NOALLOC_MAX_GRID * 2 * 128 * NOALLOC_MAX_M;
-constexpr size_t NOALLOC_PART_BYTES = NOALLOC_PART_FLOATS * sizeof(float);      // 5 MiB
+constexpr size_t NOALLOC_PART_BYTES = NOALLOC_PART_FLOATS * sizeof(float);      // 20 MiB
 constexpr size_t NOALLOC_BYTES = NOALLOC_PART_BYTES + NOALLOC_MAX_ROWS * sizeof(uint32_t);
 
 // partial sums at offset 0, row counters after them
@@ -25,9 +28,8 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
 
 constexpr int MAX_DEVICES = 64;
 struct DeviceScratch {
-    std::once_flag once;
-    unsigned char *ptr = nullptr;  // device address of g_noalloc_scratch on this device
-    cudaError_t err = cudaSuccess;
+    std::mutex mu;
+    unsigned char *ptr = nullptr;  // device address of g_noalloc_scratch on this device; set on success only
 };
 DeviceScratch g_dev[MAX_DEVICES];
 
@@ -55,28 +57,34 @@ extern "C" cloak_status cloak_linear_noalloc(cloak_ctx *ctx, int32_t tensor, con
         ctx->last_err = "cloak_linear_noalloc: tensor has more than 4096 tile rows";
         return CLOAK_E_INVAL;
     }
+    if ((uint32_t)ctx->sm_count > NOALLOC_MAX_SMS) {
+        ctx->last_err = "cloak_linear_noalloc: devices of more than 160 SMs are not supported";
+        return CLOAK_E_UNSUPPORTED;
+    }
     if (!ctx->keyed) return CLOAK_E_STATE;
     if ((flags & CLOAK_LINEAR_UNCLOAKED) && !ctx->twin) return CLOAK_E_STATE;
     if (ctx->device < 0 || ctx->device >= MAX_DEVICES) return CLOAK_E_UNSUPPORTED;
     CLOAK_CUDA(ctx, cudaSetDevice(ctx->device));
     // once per device, with that device current: the array's device address
-    // (host code cannot use the symbol itself) and zeroed row counters
+    // (host code cannot use the symbol itself). A failed look-up is not kept:
+    // the next call tries again.
     DeviceScratch &d = g_dev[ctx->device];
-    std::call_once(d.once, [&] {
-        void *p = nullptr;
-        d.err = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (d.err == cudaSuccess)
-            d.err = cudaMemset((unsigned char *)p + NOALLOC_PART_BYTES, 0,
-                               NOALLOC_MAX_ROWS * sizeof(uint32_t));
-        if (d.err == cudaSuccess) d.ptr = (unsigned char *)p;
-    });
-    if (d.err != cudaSuccess || !d.ptr) return cuda_fail(ctx, d.err, "noalloc scratch set-up");
+    unsigned char *base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(d.mu);
+        if (!d.ptr) {
+            void *p = nullptr;
+            const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess || !p) return cuda_fail(ctx, e, "noalloc scratch set-up");
+            d.ptr = (unsigned char *)p;
+        }
+        base = d.ptr;
+    }
     cudaStream_t s = (cudaStream_t)stream;
-    uint32_t *rowcnt = reinterpret_cast<uint32_t *>(d.ptr + NOALLOC_PART_BYTES);
+    uint32_t *rowcnt = reinterpret_cast<uint32_t *>(base + NOALLOC_PART_BYTES);
     // counters must start at zero; a completed call leaves them zero, an
-    // aborted one may not, so clear the ones this tensor uses
+    // aborted one or another tensor's may not, so clear the ones this tensor uses
     CLOAK_CUDA(ctx, cudaMemsetAsync(rowcnt, 0, (size_t)ctx->info[tensor].nt * sizeof(uint32_t), s));
     return linear_run_given_scratch(ctx, tensor, x_dev, y_dev, M, out_dtype, flags,
-                                    reinterpret_cast<float *>(d.ptr), NOALLOC_PART_FLOATS, rowcnt,
-                                    NOALLOC_MAX_GRID, s);
+                                    reinterpret_cast<float *>(base), NOALLOC_PART_FLOATS, rowcnt, s);
 }
