@@ -375,7 +375,13 @@ def silu(g):
     return g / (1.0 + np.exp(-g))
 
 
-def stack_decode_f64(model, W64, h0, eps=1e-5):
+def _bf16_round(x):
+    """Each value rounded to BF16 (to FP32, then to nearest even BF16) and
+    returned in FP64."""
+    return bf16_value(bf16_bits(np.asarray(x, np.float64).astype(np.float32)))
+
+
+def stack_decode_f64(model, W64, h0, eps=1e-5, bf16_operands=False):
     """One decode step of a LLaMA-style decoder stack in FP64 (the reference
     of the persistent stack launch). W64: per tensor, the weights as FP64 in
     descriptor order (q, k, v, o, gate, up, down per layer). Per layer, with
@@ -383,20 +389,25 @@ def stack_decode_f64(model, W64, h0, eps=1e-5):
       v = (h r) Wv^T; a = the value of the single token itself (softmax over
       one score is 1), query head j reading KV head j // (H / H_kv);
       h += a Wo^T; g, u = (h r') W^T; h += (silu(g) * u) Wd^T.
-    q and k do not affect a one-token step."""
+    q and k do not affect a one-token step.
+    bf16_operands: every linear takes its activation operand in BF16, as the
+    stack launch's linears do (R11: round to nearest even; the residual h
+    stays in full precision): v = R((R(h) Wv^T) r), a from R-rounded v,
+    g, u = (R(h) W^T) r', act = R(silu(g) u), where R rounds to BF16."""
     h = np.asarray(h0, np.float64).copy()
     M = h.shape[0]
     H, Hkv, hd = model.n_heads, model.n_kv_heads, model.head_dim
+    R = _bf16_round if bf16_operands else (lambda z: z)
     for l in range(model.num_layers):
         ts = {t.kind: i for i, t in enumerate(model.tensors) if t.layer == l}
         r = 1.0 / np.sqrt(np.mean(h * h, axis=1, keepdims=True) + eps)
-        v = linear_f64(h * r, W64[ts[4]])                         # kind 4 = v
+        v = R(linear_f64(R(h), W64[ts[4]]) * r)                  # kind 4 = v
         a = np.repeat(v.reshape(M, Hkv, hd), H // Hkv, axis=1).reshape(M, H * hd)
         h = h + linear_f64(a, W64[ts[5]])                         # o
         r = 1.0 / np.sqrt(np.mean(h * h, axis=1, keepdims=True) + eps)
-        g = linear_f64(h * r, W64[ts[6]])                         # gate
-        u = linear_f64(h * r, W64[ts[7]])                         # up
-        h = h + linear_f64(silu(g) * u, W64[ts[8]])               # down
+        g = linear_f64(R(h), W64[ts[6]]) * r                      # gate
+        u = linear_f64(R(h), W64[ts[7]]) * r                      # up
+        h = h + linear_f64(R(silu(g) * u), W64[ts[8]])            # down
     return h
 
 

@@ -272,3 +272,45 @@ def test_forward_with_a_wide_score_spread():
             Wn[t] = Wn[t] * math.sqrt(128)
     far = O.transformer_logits_f64(m, Wn, emb, toks)
     assert np.abs(far - got).max() > 1e-3 * np.abs(got).max()
+
+
+# ------------------------------------------- stack step with BF16 operands
+
+def _bf16(x):
+    """x rounded to FP32, then to BF16 by keeping the upper half of the FP32
+    pattern with the lower half rounded to nearest, ties to an even upper
+    half (finite inputs)."""
+    import struct
+    u = struct.unpack("<I", struct.pack("<f", float(x)))[0]
+    lo, hi = u & 0xFFFF, u >> 16
+    if lo > 0x8000 or (lo == 0x8000 and (hi & 1)):
+        hi += 1
+    return struct.unpack("<f", struct.pack("<I", (hi & 0xFFFF) << 16))[0]
+
+
+def test_stack_step_with_bf16_operands_equals_a_scalar_restatement():
+    """Two layers, two tokens: every linear input rounded to BF16 (R(h) into
+    v, gate, up; v rounded after its row scale; the SwiGLU product rounded
+    before the down projection), the residual kept in full precision."""
+    m = synth.small_decoder(2, synth.DT_BF16, d_model=256, n_heads=4, n_kv_heads=2, d_ff=192,
+                            head_dim=128)
+    W = [w.astype(np.float64) for w in synth.weights_host(m, seed=4, std=0.05)]
+    h0 = synth.activations_host(2, 256, seed=6).astype(np.float64)
+    got = O.stack_decode_f64(m, W, h0, bf16_operands=True)
+    R = np.vectorize(_bf16)
+    h = h0.copy()
+    for l in range(2):
+        q, k, v, o, g, u, d = (W[7 * l + i] for i in range(7))
+        for t in range(2):
+            r = 1.0 / math.sqrt(sum(e * e for e in h[t]) / 256 + 1e-5)
+            vv = R((v @ R(h[t])) * r)
+            a = np.concatenate([vv[(j // 2) * 128:(j // 2 + 1) * 128] for j in range(4)])
+            h[t] = h[t] + o @ a
+            r = 1.0 / math.sqrt(sum(e * e for e in h[t]) / 256 + 1e-5)
+            gg, uu = (g @ R(h[t])) * r, (u @ R(h[t])) * r
+            act = R(np.array([x / (1.0 + math.exp(-x)) for x in gg]) * uu)
+            h[t] = h[t] + d @ act
+    assert np.allclose(got, h, rtol=0, atol=1e-12 * np.abs(h).max())
+    plain = O.stack_decode_f64(m, W, h0)
+    diff = O.relative_error(got, plain)
+    assert 1e-5 < diff < 1e-2  # the roundings are there, and of BF16 size
