@@ -253,3 +253,47 @@ def test_cloaked_embedding(cloak_lib, vmm):
     assert a.cm.device_status() == 0 and b.cm.device_status() == 0
     a.close()
     b.close()
+
+
+def test_server_request_alone_equals_request_in_a_poisson_mix(cloak_lib):
+    """Continuous batching end to end: eight requests with Poisson arrivals
+    served through Server.run with at most three running at once (later ones
+    admitted mid-flight as earlier ones finish, prompts split into prefill
+    chunks that share steps with other requests' decode tokens), then each
+    request served alone. Every request's greedy tokens are the same in both,
+    and they are the FP64 full-model oracle's argmax wherever its top two
+    logits are clearly apart."""
+    m = small_served()
+    Ws = synth.weights_host(m, seed=0, std=0.05)
+    arr = synth.requests_poisson(80.0, 0.2, 1000, seed=7, prompt_median=60, prompt_sigma=0.6,
+                                 prompt_min=9, prompt_max=150)
+    work = [(a, np.asarray(p, np.int32), 3 + i % 6) for i, (a, p, _) in enumerate(arr[:8])]
+    assert len(work) == 8
+    sm = serve.ServedModel(m, kv_blocks=256, max_blocks=16, weights=Ws)
+    srv = serve.Server(sm, max_running=3, token_budget=48, rekey_period=None)
+    done, _ = srv.run(work)
+    assert len(done) == 8 and all(len(r.out) == r.max_new for r in done)
+    mixed = {r.rid: list(r.out) for r in done}
+    solo_steps = 0
+    for rid, (a, p, n) in enumerate(work):
+        solo = serve.Server(sm, max_running=3, token_budget=48, rekey_period=None)
+        d, _ = solo.run([(0.0, p, n)])
+        assert d[0].out == mixed[rid], rid
+        solo_steps += solo.steps
+    # the mix really mixed: requests shared steps
+    assert srv.steps < solo_steps, (srv.steps, solo_steps)
+    assert sm.cm.device_status() == 0
+    sm.close()
+    W64 = [O.bf16_value(O.bf16_bits(w)) for w in Ws]
+    emb64 = O.bf16_value(O.bf16_bits(synth.embedding_host(1000, 512)))
+    checked = 0
+    for rid, (a, p, n) in enumerate(work):
+        seq = list(p) + mixed[rid]
+        ref = O.transformer_logits_f64(m, W64, emb64, seq[:-1])
+        for j in range(n):
+            row = ref[len(p) - 1 + j]
+            top = np.sort(row)[-2:]
+            if top[1] - top[0] > 0.05 * np.std(row):
+                assert mixed[rid][j] == int(np.argmax(row)), (rid, j)
+                checked += 1
+    assert checked >= 20
