@@ -152,32 +152,75 @@ def barrier(ws):
 
 # ------------------------------------------------------------ oracle (CPU)
 
-def oracle_sample(model, seconds=12.0, M=1):
-    """Time the CPU oracle's cloaked linear (stored matrix read back through
-    the tables in C, then the FP64 product in NumPy) over the layer's tensors
-    in turn until `seconds` of work: returns (GB/s of weights, sample text)."""
+def _oracle_worker(arena_path, M, seconds, steps, warmup, barrier):
+    """One CPU worker of the oracle baseline (its own process, BLAS pinned to
+    one thread): the oracle's cloaked linear (stored matrix read back through
+    the tables in C, then the FP64 product in NumPy) over the 7B-class
+    layer's tensors in turn: `warmup` untimed linears, then `seconds` (or
+    `steps` linears) timed. Returns (bytes, seconds, linears timed)."""
+    import oracle as O
+    from paper_2606_18400_gb300 import synth
+    model = synth.llama7b_layer(1)
+    om = O.OracleModel(model)
+    tb = O.keygen(om, KEY, 0)
+    arena = np.load(arena_path, mmap_mode="r")
+    xs = [synth.activations_host(M, t.k, seed=1 + i) for i, t in enumerate(model.tensors)]
+    for w in range(max(1, warmup)):  # the first also pages the arena in
+        O.cloaked_linear(om, tb, w % len(model.tensors), arena, xs[w % len(model.tensors)])
+    barrier.wait()
+    done_b, n, t0 = 0, 0, time.perf_counter()
+    while True:
+        i = (warmup + n) % len(model.tensors)
+        tt = model.tensors[i]
+        O.cloaked_linear(om, tb, i, arena, xs[i])
+        done_b += tt.n * tt.k * 2 + 4 * (-(-tt.n // 128)) * (-(-tt.k // 128)) + M * (tt.n + tt.k) * 2
+        n += 1
+        el = time.perf_counter() - t0
+        if (steps and n >= steps) or (not steps and el >= seconds and n >= len(model.tensors)):
+            return done_b, el, n
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_cpu(model, M=1, seconds=8.0, steps=0, warmup=0, workers=(1, None)):
+    """Time the CPU oracle on the 7B-class layer with 1 worker and with one
+    worker per host core (processes started with spawn; each worker pinned to
+    one BLAS thread, all reading one shared arena). Returns, per worker count,
+    (GB/s of the layer's algorithmic bytes, seconds, linears, workers)."""
+    import multiprocessing as mp
     import oracle as O
     from paper_2606_18400_gb300 import synth
     om = O.OracleModel(model)
     tb = O.keygen(om, KEY, 0)
-    Ws = synth.weights_host(model, seed=0)
-    arena, scales = O.shuffle_model(om, tb, Ws)
-    del Ws
-    xs = [synth.activations_host(M, t.k, seed=1 + i) for i, t in enumerate(model.tensors)]
-    done_b, t0, n = 0, time.perf_counter(), 0
-    while True:
-        i = n % len(model.tensors)
-        tt = model.tensors[i]
-        O.cloaked_linear(om, tb, i, arena, xs[i])
-        done_b += tt.n * tt.k * 2 + M * (tt.n + tt.k) * 2
-        n += 1
-        el = time.perf_counter() - t0
-        if el >= seconds and n >= len(model.tensors):
-            break
-    return done_b / el / 1e9, el, n
+    arena, _ = O.shuffle_model(om, tb, synth.weights_host(model, seed=0))
+    out = {}
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "arena.npy")
+        np.save(path, arena)
+        del arena
+        ctx = mp.get_context("spawn")
+        for w in workers:
+            n = w or host_cores()
+            with ctx.Manager() as mgr:
+                bar = mgr.Barrier(n)
+                with ctx.Pool(n) as pool:
+                    res = pool.starmap(_oracle_worker, [(path, M, seconds, steps, warmup, bar)] * n)
+            b = sum(r[0] for r in res)
+            el = max(r[1] for r in res)
+            out[n] = (b / el / 1e9, el, sum(r[2] for r in res), n)
+    return out
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle, as it stands, on all host cores (one
+    worker process per core, each single-threaded). A step is one
+    single-tensor cloaked linear per worker, cycling over the layer's 7
+    tensors."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
@@ -185,33 +228,18 @@ def run_reference(args):
     import oracle as O
     O.build()
     model = synth.llama7b_layer(1)
-    om = O.OracleModel(model)
-    tb = O.keygen(om, KEY, 0)
-    Ws = synth.weights_host(model, seed=0)
-    arena, _ = O.shuffle_model(om, tb, Ws)
-    del Ws
     M = args.M
-    xs = [synth.activations_host(M, t.k, seed=1 + i) for i, t in enumerate(model.tensors)]
-    # a step: the oracle's cloaked linear of one tensor of the layer, in turn
-    def step(s):
-        i = s % len(model.tensors)
-        O.cloaked_linear(om, tb, i, arena, xs[i])
-        tt = model.tensors[i]
-        return tt.n * tt.k * 2 + 4 * (-(-tt.n // 128)) * (-(-tt.k // 128)) + M * (tt.n + tt.k) * 2
-    for s in range(args.warmup):
-        step(s)
-    t0 = time.perf_counter()
-    b = sum(step(args.warmup + s) for s in range(args.steps))
-    el = time.perf_counter() - t0
-    value = b / el / 1e9
-    sample = (f"{args.steps} single-tensor steps cycling over the layer's 7 tensors "
-              f"(M={M}), after {args.warmup} warm-up steps")
+    n = host_cores()
+    r = oracle_cpu(model, M=M, steps=args.steps, warmup=args.warmup, workers=(None,))[n]
+    value, el, linears, _ = r
+    sample = (f"{args.steps} timed single-tensor linears per worker after {args.warmup} untimed, "
+              f"{n} workers (one per host core), cycling over the layer's 7 tensors (M={M})")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "batch": M},
-            "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": "GB/s", "cores": n, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -238,7 +266,8 @@ def tuned_shape(r):
             "candidates": r["candidates"]}
 
 
-def bench_extras(cloak, synth, torch, dev, stream, key, steps, tune=True):
+def bench_extras(cloak, synth, torch, dev, stream, key, steps, tune=True, serve_rates=(2.0, 8.0, 32.0),
+                 serve_seconds=10.0):
     """Other rows of the hot path, each on its own context: BF16 prefill of the
     7B-class layer (M = 512, 2048), the FP8 GQA layer (decode M = 1 and
     prefill M = 2048), and the in-place re-key of the 32-layer 12.95 GB stack."""
@@ -302,6 +331,8 @@ def bench_extras(cloak, synth, torch, dev, stream, key, steps, tune=True):
     cm.close()
     torch.cuda.empty_cache()
 
+    out["fp8_peak"] = fp8_peak(torch, dev)
+
     # FP8 GQA layer (d 3584, 28/4 heads, MLP 18944), E4M3 + FP32 row scales
     model = synth.gqa28_fp8(1)
     cm = cloak.CloakModel(model, device=dev, twin=True)
@@ -320,6 +351,9 @@ def bench_extras(cloak, synth, torch, dev, stream, key, steps, tune=True):
     f8["prefill_M2048"] = {"cloaked_tflops": round(2 * wbytes * 2048 / (r["cloaked"] / 1e3) / 1e12, 1),
                            "uncloaked_tflops": round(2 * wbytes * 2048 / (r["uncloaked"] / 1e3) / 1e12, 1),
                            "launch_shape": r.get("launch_shape")}
+    pk = out["fp8_peak"].get("fp8_tflops")
+    if pk:
+        f8["prefill_M2048"]["frac_of_measured_fp8_peak"] = round(f8["prefill_M2048"]["cloaked_tflops"] / pk, 4)
     out["fp8_gqa3584_layer"] = f8
     cm.close()
     torch.cuda.empty_cache()
@@ -390,7 +424,63 @@ def bench_extras(cloak, synth, torch, dev, stream, key, steps, tune=True):
     out["keyed_upload_llama7b_layer"] = bench_upload(cloak, synth, torch, dev, key)
     out["tile_rekey_llama7b_32L"] = bench_tile_rekey(cloak, synth, torch, dev, stream, key)
     out["moe_qwen3_30b_a3b_block"] = bench_moe(cloak, synth, torch, dev, stream, key)
+    if serve_rates:
+        from paper_2606_18400_gb300 import serve
+        sw = serve_sweep(cloak, serve, synth, torch, serve_rates, serve_seconds, serve_seconds, 7000,
+                         serve_seconds)
+        out["serving_7b_32L_vocab32000"] = {
+            "workload": f"Poisson arrivals for {serve_seconds:g} s per rate (+ up to {serve_seconds:g} s "
+                        f"drain), prompts lognormal median 1024 clipped [128, 4096], outputs U[64, 1024], "
+                        f"KV pool 7000 blocks of 16 tokens, re-key every {serve_seconds:g} s on the "
+                        f"cloaked arm (concurrent)",
+            "rates": sw}
     return out
+
+
+def fp8_peak(torch, dev, n=8192, sustain_s=3.0):
+    """Dense E4M3 tensor throughput of this GPU as cuBLAS gives it (the FP8
+    denominator of the prefill roofline): torch._scaled_mm of two n x n E4M3
+    matrices (per-tensor scales 1, BF16 out), 2 n^3 FLOP per call; the best of
+    10 timed calls (burst) and the mean over back-to-back calls for
+    `sustain_s` seconds (sustained), with the clocks sampled meanwhile."""
+    try:
+        clk = ClockSampler(dev)
+        a = (torch.randn(n, n, device="cuda") * 0.5).to(torch.float8_e4m3fn)
+        b = (torch.randn(n, n, device="cuda") * 0.5).to(torch.float8_e4m3fn).t()  # column-major
+        one = torch.ones((), device="cuda", dtype=torch.float32)
+        mm = lambda: torch._scaled_mm(a, b, scale_a=one, scale_b=one, out_dtype=torch.bfloat16)
+        for _ in range(3):
+            mm()
+        torch.cuda.synchronize()
+        best = float("inf")
+        for _ in range(10):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            mm()
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        calls, e0, e1 = 0, torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < sustain_s:
+            for _ in range(20):
+                mm()
+            calls += 20
+            torch.cuda.synchronize()
+        e1.record()
+        torch.cuda.synchronize()
+        flop = 2.0 * n ** 3
+        res = {"fp8_tflops": round(flop / (best / 1e3) / 1e12, 1),
+               "fp8_tflops_sustained": round(flop * calls / (e0.elapsed_time(e1) / 1e3) / 1e12, 1),
+               "how": f"torch._scaled_mm E4M3 {n}^3, per-tensor scales, BF16 out: best of 10 calls "
+                      f"(burst), {calls} back-to-back calls (sustained)",
+               "clocks": clk.stop()}
+        del a, b
+        torch.cuda.empty_cache()
+        return res
+    except Exception as e:  # no FP8 GEMM in this torch build
+        return {"error": str(e)[:200]}
 
 
 def bench_moe(cloak, synth, torch, dev, stream, key, steps=64):
@@ -714,7 +804,10 @@ def run_cloak(args):
     hbm = peaks.get("hbm_gbs")
     peak_note = "measured" if hbm else "fallback"
     hbm = hbm or 6800.0
-    achieved = B / (kern_ms / 1e3) / 1e9
+    # a step of the timed region is one launch of the grouped kernel (graph
+    # replay): its average duration there is the kernel's launch duration over
+    # the timed region; the per-launch event brackets are kept beside it
+    achieved = B / (ms / 1e3) / 1e9
 
     # batch sweep (cloaked / uncloaked), same method
     sweep = {}
@@ -775,17 +868,26 @@ def run_cloak(args):
     moved = cm.NP * model.page_bytes
     status = cm.device_status()
     cm.close()
-    extras = None if args.no_extras else bench_extras(cloak, synth, torch, dev, stream, rank_key(rank),
-                                                      args.steps, tune=not args.no_tune)
+    extras = None if args.no_extras else bench_extras(
+        cloak, synth, torch, dev, stream, rank_key(rank), args.steps, tune=not args.no_tune,
+        serve_rates=[float(r) for r in args.bench_serve_rates.split(",")] if args.bench_serve_rates else (),
+        serve_seconds=args.bench_serve_seconds)
     clk = clocks.stop()
 
     if rank == 0:
         cpu = None
         if args.gpus == 1 and not args.no_cpu_baseline:
-            gbs, el, n = oracle_sample(model, seconds=args.cpu_seconds, M=M)
-            cpu = {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
-                   "sample": f"{n} single-tensor oracle linears (M={M}) over {el:.1f} s, "
-                             f"cycling over the layer's 7 tensors"}
+            r = oracle_cpu(model, M=M, seconds=args.cpu_seconds / 2)
+            one = r[1]
+            nc = max(r)
+            allc = r[nc]
+            cpu = {"value": allc[0], "unit": "GB/s", "cores": nc, "kind": "oracle",
+                   "sample": f"{allc[2]} single-tensor oracle linears (M={M}) by {nc} worker processes "
+                             f"(one per host core, one BLAS thread each) over {allc[1]:.1f} s, cycling "
+                             f"over the layer's 7 tensors",
+                   "host_cores": host_cores(),
+                   "single_thread": {"value": one[0], "unit": "GB/s", "cores": 1,
+                                     "sample": f"{one[2]} linears by one worker over {one[1]:.1f} s"}}
         traffic = traffic_record(os.path.join(ROOT, "paper_2606_18400_gb300", "csrc", "linear.cu"))
         line = {
             "metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": ws,
@@ -801,7 +903,10 @@ def run_cloak(args):
                          "unit": "GB/s", "frac": round(achieved / hbm, 4),
                          "traffic": traffic, "peak_source": peak_note,
                          "kernel": "k_linear_tc<bf16, N=16>: one launch, 7 linears, swap-AB tcgen05, stream-K",
-                         "kernel_us": round(kern_ms * 1e3, 2)},
+                         "kernel_us": round(ms * 1e3, 2),
+                         "kernel_us_source": "CUDA events around the timed region's graph replays "
+                                             "(one launch of the kernel per step), divided by the steps",
+                         "kernel_us_bracketed": round(kern_ms * 1e3, 2)},
             "cpu_baseline": cpu,
             "e2e": {"value": round(job_rate(B, e2e_ms, ws) / 1e9, 2), "unit": "GB/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -824,43 +929,60 @@ def run_cloak(args):
         dist.destroy_process_group()
 
 
+def serve_sweep(cloak, serve, synth, torch, rates, seconds, drain, kv_blocks, rekey_period,
+                rekey_between=False):
+    """Serving workload on the 32-layer cloaked BF16 model with a 32,000-token
+    lm_head: Poisson arrivals for `seconds` at each rate, lognormal prompts
+    clipped to [128, 4096], outputs uniform in [64, 1024], continuous batching
+    admitted by free KV blocks (up to `drain` more seconds to finish), a
+    re-key every `rekey_period` s on the cloaked arm (concurrent: copies on a
+    side stream, tables published between steps); cloaked and uncloaked arms
+    on the same arrivals. Throughput counts every sampled token over the wall
+    time; latencies are those of the requests that got their tokens."""
+    model = synth.serving_model(32, 32000)
+    sm = serve.ServedModel(model, kv_blocks=kv_blocks, max_blocks=(4096 + 1024) // 16 + 1, twin=True)
+    results = {}
+    for rate in rates:
+        work = synth.requests_poisson(rate, seconds, 32000, seed=int(rate * 10))
+        offered = sum(w[2] for w in work) / seconds
+        row = {"requests_arrived": len(work), "offered_tokens_per_s": round(offered, 1)}
+        for name, unc in (("cloaked", False), ("uncloaked", True)):
+            # the plain model has nothing to re-key
+            srv = serve.Server(sm, max_running=64, token_budget=2048, uncloaked=unc,
+                               rekey_period=None if unc else rekey_period,
+                               rekey_concurrent=not rekey_between)
+            done, wall = srv.run(work, max_wall=seconds + drain)
+            st = serve.latency_stats(done, wall)
+            st["tokens_per_s"] = srv.tokens_out / wall
+            st["tokens"] = srv.tokens_out
+            st["steps"] = srv.steps
+            st["mean_step_tokens"] = float(np.mean(srv.step_tokens)) if srv.step_tokens else 0.0
+            st["rekeys"] = [{k: (round(v, 3) if isinstance(v, float) else v) for k, v in r.items()}
+                            for r in srv.rekeys]
+            row[name] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in st.items()}
+        c, u = row["cloaked"], row["uncloaked"]
+        row["cloaked_vs_uncloaked_tokens_pct"] = round((c["tokens_per_s"] / u["tokens_per_s"] - 1) * 100, 2)
+        # saturated: requests were still queued or running when the window
+        # closed, or waited seconds for their first token
+        row["saturated"] = bool(u["requests"] < len(work) or (u["ttft_p99_s"] or 0.0) > 1.0)
+        results[str(rate)] = row
+    assert sm.cm.device_status() == 0
+    sm.close()
+    torch.cuda.empty_cache()
+    return results
+
+
 def run_serve(args):
-    """Serving workload: the 32-layer cloaked BF16 model with a 32,000-token
-    lm_head, Poisson arrivals, lognormal prompts clipped to [128, 4096],
-    outputs uniform in [64, 1024], continuous batching admitted by free KV
-    blocks, re-key every 30 s (concurrent: copies on a side stream, tables
-    published between steps); cloaked vs uncloaked at the same
-    arrival rates. One JSON line per run of the whole sweep."""
+    """The serving sweep alone (one JSON line)."""
     import torch
     from paper_2606_18400_gb300 import cloak, serve, synth
     cloak.load()
     torch.cuda.set_device(0)
-    model = synth.serving_model(32, 32000)
-    sm = serve.ServedModel(model, kv_blocks=args.kv_blocks, max_blocks=(4096 + 1024) // 16 + 1, twin=True)
     rates = [float(r) for r in args.rates.split(",")]
-    results = {}
     clocks = ClockSampler(0)
-    for rate in rates:
-        work = synth.requests_poisson(rate, args.serve_seconds, 32000, seed=int(rate * 10))
-        row = {}
-        for name, unc in (("cloaked", False), ("uncloaked", True)):
-            # the plain model has nothing to re-key
-            srv = serve.Server(sm, max_running=64, token_budget=2048, uncloaked=unc,
-                               rekey_period=None if unc else args.rekey_period,
-                               rekey_concurrent=not args.rekey_between_steps)
-            done, wall = srv.run(work, max_wall=args.serve_seconds + args.drain_seconds)
-            st = serve.latency_stats(done, wall)
-            st["submitted"] = len(work)
-            st["steps"] = srv.steps
-            st["mean_step_tokens"] = float(np.mean(srv.step_tokens)) if srv.step_tokens else 0.0
-            st["rekeys"] = len(srv.rekeys)
-            st["rekey_detail"] = [{k: (round(v, 3) if isinstance(v, float) else v) for k, v in r.items()}
-                                  for r in srv.rekeys]
-            row[name] = st
-        results[str(rate)] = row
+    results = serve_sweep(cloak, serve, synth, torch, rates, args.serve_seconds, args.drain_seconds,
+                          args.kv_blocks, args.rekey_period, args.rekey_between_steps)
     clk = clocks.stop()
-    assert sm.cm.device_status() == 0
-    sm.close()
     tps = {r: results[r]["cloaked"]["tokens_per_s"] for r in results}
     line = {"metric": "serving tokens/s (cloaked 7B-class BF16 model, continuous batching)",
             "value": max(tps.values()), "unit": "tokens/s", "n_gpus": 1,
@@ -878,7 +1000,7 @@ def run_serve(args):
 
 def run_profile(args):
     """Small cases of one kernel each, for ncu captures (a few GB at most):
-    stack  -- a 4-layer 7B-class stack (1.6 GB), decode M=1, 3 launches;
+    stack  -- a 4-layer 7B-class stack (1.6 GB), decode of --M tokens (default 1), 3 launches;
     fp8    -- one GQA E4M3 layer (233 MB), grouped decode M=1, 3 launches;
     fp8prefill -- the same layer, grouped prefill M=2048 (the prefill GEMM), 3 launches;
     prefill-- one 7B-class layer, grouped M=2048 (the prefill GEMM), 3 launches;
@@ -917,7 +1039,7 @@ def run_profile(args):
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
     elif args.profile == "stack":
-        h0 = torch.from_numpy(synth.activations_host(1, 4096, seed=1)).cuda()
+        h0 = torch.from_numpy(synth.activations_host(args.M, 4096, seed=1)).cuda()
         torch.cuda.nvtx.range_push("profiled")
         for _ in range(3):
             cm.stack_decode(h0.clone())
@@ -956,6 +1078,9 @@ def main():
     ap.add_argument("--profile", choices=["stack", "fp8", "fp8prefill", "prefill", "decode", "moe"],
                     help="small case for ncu")
     ap.add_argument("--rates", default="2,8,32")
+    ap.add_argument("--bench-serve-rates", default="2,8,32",
+                    help="arrival rates of the serving sweep in the extras ('' to skip)")
+    ap.add_argument("--bench-serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-seconds", type=float, default=30.0)
     ap.add_argument("--drain-seconds", type=float, default=30.0)
     ap.add_argument("--kv-blocks", type=int, default=7000)

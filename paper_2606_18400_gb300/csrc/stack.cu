@@ -31,13 +31,17 @@
 namespace cloak {
 
 enum { MODE_SCALED = 0, MODE_RESID = 1, MODE_SWIGLU = 2 };
-// Split tile rows are summed in one of two ways. Up to 16 tokens: by the CTA
-// holding the row's first tiles, from tagged words (below). Wider batches: by
-// the CTA that arrives last on the row's counter, from FP32 pieces; there the
-// finaliser's reads, not the hand-off, dominate, and plain floats halve them.
+// Split tile rows are summed in one of two ways, both in CTA order (so the two
+// give the same bits). Up to 4 tokens: by the CTA holding the row's first
+// tiles, from tagged words (below); no counter sits between the pieces and the
+// sum. Wider batches: every CTA holding a piece stores it as FP32 and arrives
+// on the row's counter; at the end of the stage the row's CTAs reduce it
+// together, each a share of the row's (token group, row quarter) items, so no
+// single CTA sums a whole wide row while the grid waits for it at the barrier.
 // Tokens per accumulator row in the tagged buffer, whatever the batch: a
 // word's address always means the same (CTA, gate/up, row, token).
 constexpr int PSTRIDE = 16;
+constexpr int STACK_TAG_MAX_M = 4;  // largest batch summed from tagged words (measured crossover)
 enum { XMAP_H = 0, XMAP_V = 1, XMAP_ACT = 2 };
 
 struct StackProb {
@@ -67,9 +71,9 @@ struct StackArgs {
     float *h;                 // FP32 residual [M, D]
     __nv_bfloat16 *hb;        // its BF16 copy (the activation operand)
     unsigned long long *part; // [grid][2 gate/up][128][PSTRIDE] tagged partial sums (M <= 16)
-    float *partf;             // [grid][2 pieces][2 gate/up][128][NPAD] partial sums (M > 16)
+    float *partf;             // [grid][2 slots][2 gate/up][NPAD/4 groups][128 rows][4] partial sums (M > 16)
     const uint32_t *epoch;    // tag of this launch (advanced by k_stack_input)
-    float *ss_rows;           // [D/128][64]: per residual row tile, its sum of squares per token
+    float *ss_rows;           // [D/128][4][64]: per residual row tile and row quarter, its sum of squares per token
     const float *ss_init;     // [64]: sum of squares of the input residual
     unsigned int *bar;        // grid barrier arrivals (zeroed before launch)
     int *abort;               // set by a CTA that gave up (zeroed before launch)
@@ -189,22 +193,22 @@ __device__ __forceinline__ void st_release_cta(uint32_t *p, uint32_t v) {
 
 __device__ __forceinline__ float silu(float g) { return g / (1.0f + expf(-g)); }
 
-// Sum of squares of a finalised residual row tile for tokens c0..c0+ncol-1
-// (hsq[j]: this thread's row, 0 where it wrote nothing): warp sums, then the
-// four warps in fixed order, stored for the tile. Each (tile, token) has one
-// writer per stage, so the result does not depend on which CTA it is.
-__device__ __forceinline__ void tile_squares(float (&hsq)[16], int c0, int ncol, int qd, int lane, int et,
-                                             float *ss_w, float *dst) {
+// Sums of squares of a finalised residual quarter tile (this warp's 32 rows)
+// for tokens c0..c0+ncol-1 (hsq[j]: this thread's row, 0 where it wrote
+// nothing): a warp butterfly per token, stored by lane 0 as the quarter's
+// entry of the tile (dst: [64] tokens). Each (tile, quarter, token) has one
+// writer per stage, so the result does not depend on which CTA it is; the
+// norm adds the four quarters of a tile in order, then the tiles in order.
+template <int NJ>
+__device__ __forceinline__ void quarter_squares(float (&hsq)[NJ], int c0, int ncol, int lane, float *dst) {
 #pragma unroll
-    for (int j = 0; j < 16; ++j)
+    for (int j = 0; j < NJ; ++j)
         for (int o = 16; o; o >>= 1) hsq[j] += __shfl_xor_sync(0xffffffffu, hsq[j], o);
     if (lane == 0) {
 #pragma unroll
-        for (int j = 0; j < 16; ++j) ss_w[qd * 16 + j] = hsq[j];
+        for (int j = 0; j < NJ; ++j)
+            if (j < ncol) dst[c0 + j] = hsq[j];
     }
-    asm volatile("bar.sync 1, 128;" ::: "memory");
-    if (et < ncol) dst[c0 + et] = ss_w[et] + ss_w[16 + et] + ss_w[32 + et] + ss_w[48 + et];
-    asm volatile("bar.sync 1, 128;" ::: "memory");
 }
 
 // Tagged partial sums: one 64-bit word per value, the launch tag in the high
@@ -249,6 +253,28 @@ __device__ __forceinline__ unsigned long long *piece_word(const StackArgs &a, ui
     return a.part + (((uint64_t)c * 2 + up) * 128 + r) * PSTRIDE + m;
 }
 
+// The CTA ranges [c T / G, (c + 1) T / G) of a stage, walked in CTA order with
+// additions only (T = qt G + rt): one division to start, none per step.
+struct RangeWalk {
+    uint64_t lo, rem;  // c T / G and c T mod G
+    uint32_t c;
+    __device__ __forceinline__ void start(uint32_t c0, uint64_t T, uint64_t G) {
+        c = c0;
+        const uint64_t p = (uint64_t)c0 * T;
+        lo = p / G;
+        rem = p - lo * G;
+    }
+    __device__ __forceinline__ uint64_t hi(uint64_t qt, uint64_t rt, uint64_t G) const {
+        return lo + qt + ((rem + rt >= G) ? 1 : 0);
+    }
+    __device__ __forceinline__ void next(uint64_t qt, uint64_t rt, uint64_t G) {
+        const uint64_t r2 = rem + rt;
+        lo += qt + ((r2 >= G) ? 1 : 0);
+        rem = (r2 >= G) ? r2 - G : r2;
+        ++c;
+    }
+};
+
 // The finaliser of a split tile row adds, in CTA order, the pieces that the
 // CTAs after it hold of the row, for tokens c0 .. c0+ncol-1 (c0 even) of
 // this thread's accumulator row r_in. v0 is the end of this CTA's range, where
@@ -260,11 +286,13 @@ __device__ __forceinline__ void add_pieces(const StackArgs &a, float (&vg)[16], 
                                            uint64_t v0, uint64_t re, uint64_t T, int c0, int ncol,
                                            int r_in, uint32_t tag) {
     constexpr int IB = PAIRED ? 4 : 8;
-    const uint64_t G = gridDim.x;
+    const uint64_t G = gridDim.x, qt = T / G, rt = T - qt * G;
     const int ng = (ncol + 3) >> 2;  // four-token groups of the chunk
     int q_have = -1;                  // piece whose CTA is in 'cta'
     uint32_t cta = 0;
-    uint64_t v = v0;                  // first unit of piece q_have + 1
+    RangeWalk w;                      // the CTA after this one: its range begins at v0
+    w.start(blockIdx.x + 1, T, G);
+    (void)v0;
     int total = -1;                   // items of the row, once the walk has ended
     for (int base = 0;; base += IB) {
         unsigned long long eg[IB][4], eu[IB][4];
@@ -275,9 +303,10 @@ __device__ __forceinline__ void add_pieces(const StackArgs &a, float (&vg)[16], 
             const int item = base + k;
             const int q = item / ng, g = item - q * ng;
             if (q > q_have && total < 0) {
-                if (v < re) {
-                    cta = cta_of_unit(v, G, T);
-                    v = ((uint64_t)cta + 1) * T / G;
+                while (w.lo < re && w.hi(qt, rt, G) == w.lo) w.next(qt, rt, G);  // empty ranges
+                if (w.lo < re) {
+                    cta = w.c;
+                    w.next(qt, rt, G);
                     q_have = q;
                 } else {
                     total = q * ng;
@@ -333,44 +362,131 @@ __device__ __forceinline__ void add_pieces(const StackArgs &a, float (&vg)[16], 
     }
 }
 
-// Sum, in CTA order, the FP32 pieces that CTAs c_first..c_last hold of a
-// split row (c_first's in slot ps_first, the others' in slot 0), tokens
-// c0..c0+15 of accumulator row r_in; the loads of PB pieces are in flight at
-// once.
-template <int NPAD, bool PAIRED>
-__device__ __forceinline__ void sum_pieces(const StackArgs &a, float (&ag)[16], float (&au)[16], uint32_t c_first,
-                                           uint32_t c_last, int ps_first, uint64_t T, int r_in, int c0) {
-    constexpr int PB = 2;  // pieces whose loads are in flight at once
-    const uint64_t G = gridDim.x;
-    for (uint32_t cb = c_first; cb <= c_last; cb += PB) {
-        float4 vg4[PB][4], vu4[PB][4];
-        bool has[PB];
+// FP32 piece of a split tile row (batches over 16 tokens): CTA c's piece in
+// slot 0 (the row its range begins in) or 1 (the row its range ends in),
+// gate/up accumulator acc, four-token group g, accumulator row r; the four
+// tokens are one float4, and the rows of a group are contiguous, so a warp's
+// 32 rows of one group are 512 consecutive bytes.
+template <int NPAD>
+__device__ __forceinline__ float *piece_f(const StackArgs &a, uint32_t c, int slot, int acc, int g, int r) {
+    return a.partf + (((((uint64_t)c * 2 + slot) * 2 + acc) * (NPAD / 4) + g) * 128 + r) * 4;
+}
+
+// Outputs of four-token group g of accumulator row r_in of tile row nt
+// (sg, su: the row's sums; hv: the residual's old values), with the residual
+// quarter's sums of squares.
+__device__ __forceinline__ void emit_group(const StackArgs &a, const StackProb &P, uint32_t nt, int g, int r_in,
+                                           const float (&sg)[4], const float (&su)[4], const float (&hv)[4],
+                                           const float *rstd, int qd, int lane) {
+    const int row = (int)(nt * 128) + r_in;
+    const int c0 = 4 * g, ncol = min(4, a.M - c0);
+    float hsq[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    if (row < P.N) {
 #pragma unroll
-        for (int q = 0; q < PB; ++q) {
-            const uint32_t c = cb + q;
-            has[q] = c <= c_last && ((uint64_t)c * T / G < ((uint64_t)c + 1) * T / G);
-            if (!has[q]) continue;
-            const int ps = (c == c_first) ? ps_first : 0;
-            const float *pp = a.partf + ((((uint64_t)c * 2 + ps) * 2) * 128 + r_in) * NPAD + c0;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                vg4[q][j] = __ldcg(reinterpret_cast<const float4 *>(pp) + j);
-                if (PAIRED) vu4[q][j] = __ldcg(reinterpret_cast<const float4 *>(pp + 128 * NPAD) + j);
+        for (int j = 0; j < 4; ++j) {
+            if (j >= ncol) continue;
+            const int m = c0 + j;
+            const size_t o = (size_t)m * P.N + row;
+            if (P.mode == MODE_SCALED) {
+                P.out[o] = __float2bfloat16_rn(sg[j] * rstd[m]);
+            } else if (P.mode == MODE_RESID) {
+                const float hn = hv[j] + sg[j];
+                a.h[o] = hn;
+                a.hb[o] = __float2bfloat16_rn(hn);
+                hsq[j] = hn * hn;
+            } else {
+                P.out[o] = __float2bfloat16_rn(silu(sg[j] * rstd[m]) * (su[j] * rstd[m]));
             }
         }
+    }
+    if (P.mode == MODE_RESID) quarter_squares(hsq, c0, ncol, lane, a.ss_rows + ((size_t)nt * 4 + qd) * 64);
+}
+
+// A split tile row this CTA holds a piece of: units [rs, re) of problem p.
+struct SplitRow {
+    int p;
+    uint32_t nt;
+    uint64_t rs, re;
+};
+
+// This CTA's share of the cooperative reduction of split row R (batches over
+// 16 tokens). The row's pieces are those of the CTAs whose ranges meet
+// [rs, re), in CTA order; k of them. The row's items (4-token group g, row
+// quarter q; item 4g + q) are cut into k contiguous shares, and the j-th
+// piece holder takes the j-th. Warp q sums, for each of its groups, every
+// piece in CTA order (GB groups and KP pieces of loads in flight at once),
+// then writes the group's outputs. Pieces are complete: the caller waited for
+// the row's counter to reach k.
+template <int NPAD, bool PAIRED>
+__device__ __forceinline__ void reduce_share(const StackArgs &a, const StackProb &P, const SplitRow &R,
+                                             uint64_t T, const float *rstd, int qd, int lane) {
+    constexpr int GB = PAIRED ? 2 : 4;  // groups per batch
+    constexpr int KP = 4;               // pieces per batch
+    const uint64_t G = gridDim.x, qt = T / G, rt = T - qt * G;
+    const int r_in = qd * 32 + lane;
+    RangeWalk w0;
+    w0.start(cta_of_unit(R.rs, G, T), T, G);
+    int k = 0, j = -1;
+    for (RangeWalk w = w0; w.lo < R.re; w.next(qt, rt, G)) {
+        if (w.hi(qt, rt, G) == w.lo) continue;  // an empty range holds no piece
+        if (w.c == blockIdx.x) j = k;
+        ++k;
+    }
+    if (j < 0) return;
+    const int ng = (a.M + 3) >> 2, ni = 4 * ng;
+    const int lo = (int)((int64_t)j * ni / k), hi = (int)((int64_t)(j + 1) * ni / k);
+    const int g_lo = lo > qd ? (lo - qd + 3) >> 2 : 0, g_hi = hi > qd ? (hi - qd + 3) >> 2 : 0;
+    const int row = (int)(R.nt * 128) + r_in;
+#pragma unroll 1
+    for (int gc = g_lo; gc < g_hi; gc += GB) {
+        float hv[GB][4], sg[GB][4], su[GB][4];
 #pragma unroll
-        for (int q = 0; q < PB; ++q) {
-            if (!has[q]) continue;
+        for (int gi = 0; gi < GB; ++gi)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                ag[4 * j] += vg4[q][j].x; ag[4 * j + 1] += vg4[q][j].y;
-                ag[4 * j + 2] += vg4[q][j].z; ag[4 * j + 3] += vg4[q][j].w;
-                if (PAIRED) {
-                    au[4 * j] += vu4[q][j].x; au[4 * j + 1] += vu4[q][j].y;
-                    au[4 * j + 2] += vu4[q][j].z; au[4 * j + 3] += vu4[q][j].w;
+            for (int t = 0; t < 4; ++t) {
+                const int m = 4 * (gc + gi) + t;
+                hv[gi][t] = (P.mode == MODE_RESID && gc + gi < g_hi && m < a.M && row < P.N)
+                                ? a.h[(size_t)m * P.N + row] : 0.0f;
+                sg[gi][t] = su[gi][t] = 0.0f;
+            }
+        RangeWalk w = w0;
+        while (w.lo < R.re) {
+            float4 vg[GB][KP], vu[GB][KP];
+            bool has[KP];
+#pragma unroll
+            for (int pi = 0; pi < KP; ++pi) {
+                while (w.lo < R.re && w.hi(qt, rt, G) == w.lo) w.next(qt, rt, G);
+                has[pi] = w.lo < R.re;
+                if (!has[pi]) continue;
+                const uint32_t c = w.c;
+                const int slot = (w.lo >= R.rs) ? 0 : 1;
+                w.next(qt, rt, G);
+#pragma unroll
+                for (int gi = 0; gi < GB; ++gi) {
+                    if (gc + gi >= g_hi) continue;
+                    vg[gi][pi] = __ldcg(reinterpret_cast<const float4 *>(piece_f<NPAD>(a, c, slot, 0, gc + gi, r_in)));
+                    if (PAIRED)
+                        vu[gi][pi] = __ldcg(reinterpret_cast<const float4 *>(piece_f<NPAD>(a, c, slot, 1, gc + gi, r_in)));
+                }
+            }
+#pragma unroll
+            for (int pi = 0; pi < KP; ++pi) {
+                if (!has[pi]) continue;
+#pragma unroll
+                for (int gi = 0; gi < GB; ++gi) {
+                    if (gc + gi >= g_hi) continue;
+                    sg[gi][0] += vg[gi][pi].x; sg[gi][1] += vg[gi][pi].y;
+                    sg[gi][2] += vg[gi][pi].z; sg[gi][3] += vg[gi][pi].w;
+                    if (PAIRED) {
+                        su[gi][0] += vu[gi][pi].x; su[gi][1] += vu[gi][pi].y;
+                        su[gi][2] += vu[gi][pi].z; su[gi][3] += vu[gi][pi].w;
+                    }
                 }
             }
         }
+#pragma unroll
+        for (int gi = 0; gi < GB; ++gi)
+            if (gc + gi < g_hi) emit_group(a, P, R.nt, gc + gi, r_in, sg[gi], su[gi], hv[gi], rstd, qd, lane);
     }
 }
 
@@ -379,8 +495,7 @@ __device__ __forceinline__ void sum_pieces(const StackArgs &a, float (&ag)[16], 
 // residual update with the tile's sums of squares, or SwiGLU.
 __device__ __forceinline__ void emit_chunk(const StackArgs &a, const StackProb &P, uint32_t nt, int c0,
                                            int ncol, int r_in, const float (&vg)[16], const float (&vu)[16],
-                                           const float (&hv)[16], const float *rstd, int qd, int lane, int et,
-                                           float *ss_w) {
+                                           const float (&hv)[16], const float *rstd, int qd, int lane) {
     const int row = (int)(nt * 128) + r_in;
     float hsq[16];
 #pragma unroll
@@ -403,7 +518,7 @@ __device__ __forceinline__ void emit_chunk(const StackArgs &a, const StackProb &
             }
         }
     }
-    if (P.mode == MODE_RESID) tile_squares(hsq, c0, ncol, qd, lane, et, ss_w, a.ss_rows + (size_t)nt * 64);
+    if (P.mode == MODE_RESID) quarter_squares(hsq, c0, ncol, lane, a.ss_rows + ((size_t)nt * 4 + qd) * 64);
 }
 
 // The residual's old values of tokens c0 .. c0+ncol-1 of tile row nt (zero
@@ -416,7 +531,7 @@ __device__ __forceinline__ void load_resid(const StackArgs &a, const StackProb &
         hv[j] = (P.mode == MODE_RESID && j < ncol && row < P.N) ? a.h[(size_t)(c0 + j) * P.N + row] : 0.0f;
 }
 
-template <int NPAD>
+template <int NPAD, bool TAGGED>
 __global__ void __launch_bounds__(192, 1)
     k_stack_tc(const __grid_constant__ CUtensorMap tw, const __grid_constant__ StackMaps xm,
                const __grid_constant__ StackArgs a) {
@@ -433,7 +548,6 @@ __global__ void __launch_bounds__(192, 1)
     uint32_t *stage_open = tmem_slot + 2;  // highest stage whose inputs are complete
     volatile uint32_t *ok_flag = tmem_slot + 3;  // end of a stage: no CTA gave up
     float *rstd = reinterpret_cast<float *>(tmem_slot + 4);  // [NPAD]
-    float *ss_w = rstd + 64;                                   // [4][16] per-warp chunk sums
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint64_t G = gridDim.x;
@@ -671,14 +785,17 @@ __global__ void __launch_bounds__(192, 1)
                         ss = a.ss_init[et];
                     } else {
                         const int ntiles = a.D / 128;
-#pragma unroll 8
-                        for (int t = 0; t < ntiles; ++t) ss += __ldcg(a.ss_rows + (size_t)t * 64 + et);
+#pragma unroll 4
+                        for (int t = 0; t < ntiles; ++t) {
+                            const float *q4 = a.ss_rows + (size_t)t * 4 * 64 + et;
+                            ss += ((__ldcg(q4) + __ldcg(q4 + 64)) + __ldcg(q4 + 128)) + __ldcg(q4 + 192);
+                        }
                     }
                     rstd[et] = rsqrtf(ss / (float)a.D + a.eps);
                 }
                 asm volatile("bar.sync 1, 128;" ::: "memory");
             }
-            if constexpr (NPAD == 16) {
+            if constexpr (TAGGED) {
                 for (uint64_t u = u0; u < u1; ++seg) {
                     const SLoc l = sloc(st, u);
                     const StackProb &P = st.p[l.p];
@@ -721,17 +838,21 @@ __global__ void __launch_bounds__(192, 1)
                             if (paired) add_pieces<NPAD, true>(a, vg, vu, u1, re, T, 0, a.M, r_in, tag);
                             else add_pieces<NPAD, false>(a, vg, vu, u1, re, T, 0, a.M, r_in, tag);
                         }
-                        emit_chunk(a, P, l.nt, 0, a.M, r_in, vg, vu, hv, rstd, qd, lane, et, ss_w);
+                        emit_chunk(a, P, l.nt, 0, a.M, r_in, vg, vu, hv, rstd, qd, lane);
                     }
                     tc_fence_before();
                     mbar_arrive(&tempty[bf]);
                     u = send;
                 }
             } else {
-                // wider batches: pieces as FP32 in per-CTA slots (0: the first
-                // segment's row, 1: the last), summed in CTA order by the CTA
-                // that arrives last on the row's counter
-                const SLoc first = (u0 < u1) ? sloc(st, u0) : SLoc{0, 0, 0, 0, 0};
+                // wider batches: every CTA holding a piece of a split tile row
+                // stores it (FP32; slot 0 for its range's first segment, 1 for
+                // its last) and arrives on the row's counter; once the stage's
+                // pieces are all out, the row's CTAs reduce it together, each
+                // taking its share of the row's items and summing every piece in
+                // CTA order, so the sums do not depend on who adds them
+                SplitRow rows[2];
+                int nrows = 0;
                 for (uint64_t u = u0; u < u1; ++seg) {
                     const SLoc l = sloc(st, u);
                     const StackProb &P = st.p[l.p];
@@ -745,8 +866,7 @@ __global__ void __launch_bounds__(192, 1)
                     bar_wait(a, &tfull[bf], use & 1);  // a timeout sets the abort word
                     tc_fence_after();
                     const uint32_t tbase = tmem + ((uint32_t)(qd * 32) << 16) + bf * 2 * NPAD;
-                    const int pslot = (l.p == first.p && l.nt == first.nt) ? 0 : 1;
-                    float *mypart = a.partf + ((((uint64_t)blockIdx.x * 2 + pslot) * 2) * 128 + r_in) * NPAD;
+                    const int slot = (u == u0) ? 0 : 1;
 #pragma unroll 1
                     for (int c0 = 0; c0 < a.M; c0 += 16) {
                         const int ncol = min(16, a.M - c0);
@@ -760,14 +880,16 @@ __global__ void __launch_bounds__(192, 1)
                             if (!paired || !has_u) vu[j] = 0.0f;
                         }
                         if (full_row) {
-                            emit_chunk(a, P, l.nt, c0, ncol, r_in, vg, vu, hv, rstd, qd, lane, et, ss_w);
+                            emit_chunk(a, P, l.nt, c0, ncol, r_in, vg, vu, hv, rstd, qd, lane);
                         } else {
 #pragma unroll
                             for (int j = 0; j < 16; j += 4) {
-                                __stcg(reinterpret_cast<float4 *>(mypart + c0 + j),
+                                if (c0 + j >= a.M) break;
+                                const int g = (c0 + j) >> 2;
+                                __stcg(reinterpret_cast<float4 *>(piece_f<NPAD>(a, blockIdx.x, slot, 0, g, r_in)),
                                        make_float4(vg[j], vg[j + 1], vg[j + 2], vg[j + 3]));
                                 if (paired)
-                                    __stcg(reinterpret_cast<float4 *>(mypart + 128 * NPAD + c0 + j),
+                                    __stcg(reinterpret_cast<float4 *>(piece_f<NPAD>(a, blockIdx.x, slot, 1, g, r_in)),
                                            make_float4(vu[j], vu[j + 1], vu[j + 2], vu[j + 3]));
                             }
                         }
@@ -775,35 +897,48 @@ __global__ void __launch_bounds__(192, 1)
                     tc_fence_before();
                     mbar_arrive(&tempty[bf]);
                     if (!full_row) {
+                        // the piece is out: every epilogue thread's stores, then
+                        // one release arrival on the row's counter
                         asm volatile("bar.sync 1, 128;" ::: "memory");
-                        const uint32_t c_first = cta_of_unit(rs, G, T), c_last = cta_of_unit(re - 1, G, T);
                         if (et == 0) {
-                            // CTAs in [c_first, c_last] with an empty range (a stage
-                            // with fewer units than CTAs) hold no piece of the row
-                            uint32_t pieces = 0;
-                            for (uint32_t c = c_first; c <= c_last; ++c)
-                                pieces += ((uint64_t)c * T / G < ((uint64_t)c + 1) * T / G) ? 1u : 0u;
-                            const uint32_t old = atom_add_acq_rel(P.rowcnt + l.nt, 1u);
-                            *last_flag = (old == pieces - 1) ? 1u : 0u;
+                            __threadfence();
+                            atomicAdd(P.rowcnt + l.nt, 1u);
                         }
-                        asm volatile("bar.sync 1, 128;" ::: "memory");
-                        if (*last_flag) {
-                            const int ps_first = ((uint64_t)c_first * T / G < rs) ? 1 : 0;
-#pragma unroll 1
-                            for (int c0 = 0; c0 < a.M; c0 += 16) {
-                                const int ncol = min(16, a.M - c0);
-                                float hv[16], ag[16], au[16];
-#pragma unroll
-                                for (int j = 0; j < 16; ++j) ag[j] = au[j] = 0.0f;
-                                if (paired) sum_pieces<NPAD, true>(a, ag, au, c_first, c_last, ps_first, T, r_in, c0);
-                                else sum_pieces<NPAD, false>(a, ag, au, c_first, c_last, ps_first, T, r_in, c0);
-                                load_resid(a, P, l.nt, c0, ncol, r_in, hv);  // 16 loads in flight at once
-                                emit_chunk(a, P, l.nt, c0, ncol, r_in, ag, au, hv, rstd, qd, lane, et, ss_w);
-                            }
-                            if (et == 0) P.rowcnt[l.nt] = 0;  // ready for the next launch
-                        }
+                        rows[nrows++] = SplitRow{l.p, l.nt, rs, re};
                     }
                     u = send;
+                }
+                // the reductions: wait until every piece of the rows is out (one
+                // poller per row), then this CTA's shares
+                if (nrows > 0) {
+                    const int wi = et >> 5;  // warp 0 polls the first row, warp 1 the second
+                    if ((et & 31) == 0 && wi < nrows) {
+                        const SplitRow &R = rows[wi];
+                        const StackProb &P = st.p[R.p];
+                        const uint64_t qt = T / G, rt = T - qt * G;
+                        RangeWalk w;
+                        w.start(cta_of_unit(R.rs, G, T), T, G);
+                        uint32_t k = 0;
+                        for (; w.lo < R.re; w.next(qt, rt, G)) k += (w.hi(qt, rt, G) > w.lo) ? 1u : 0u;
+                        if (ld_acquire(P.rowcnt + R.nt) < k) {
+                            const unsigned long long t0 = globaltimer();
+                            while (ld_acquire(P.rowcnt + R.nt) < k) {
+                                if (aborted(a.abort)) break;
+                                if (globaltimer() - t0 > WAIT_LIMIT_NS) {
+                                    give_up(a);
+                                    break;
+                                }
+                            }
+                        }
+                    }
+                    asm volatile("bar.sync 1, 128;" ::: "memory");
+                    if (!aborted(a.abort)) {
+                        for (int i = 0; i < nrows; ++i) {
+                            const StackProb &P = st.p[rows[i].p];
+                            if (P.mode == MODE_SWIGLU) reduce_share<NPAD, true>(a, P, rows[i], T, rstd, qd, lane);
+                            else reduce_share<NPAD, false>(a, P, rows[i], T, rstd, qd, lane);
+                        }
+                    }
                 }
             }
             // this CTA's outputs of the stage are written (and, after a residual
@@ -857,11 +992,11 @@ __global__ void k_stack_input(const float *h, int D, __nv_bfloat16 *hb, float *s
     }
 }
 
-template <int NPAD>
+template <int NPAD, bool TAGGED>
 static cloak_status launch_stack(cloak_ctx *ctx, const CUtensorMap &tw, const StackMaps &xm,
                                  const StackArgs &a, cudaStream_t s) {
     using C = StackCfg<NPAD>;
-    CLOAK_CUDA(ctx, cudaFuncSetAttribute(k_stack_tc<NPAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    CLOAK_CUDA(ctx, cudaFuncSetAttribute(k_stack_tc<NPAD, TAGGED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          C::SMEM));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)ctx->sm_count);
@@ -873,7 +1008,7 @@ static cloak_status launch_stack(cloak_ctx *ctx, const CUtensorMap &tw, const St
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    CLOAK_CUDA(ctx, cudaLaunchKernelEx(&cfg, k_stack_tc<NPAD>, tw, xm, a));
+    CLOAK_CUDA(ctx, cudaLaunchKernelEx(&cfg, k_stack_tc<NPAD, TAGGED>, tw, xm, a));
     CLOAK_LAUNCHED(ctx);
     return CLOAK_OK;
 }
@@ -911,7 +1046,7 @@ cloak_status stack_decode_run(cloak_ctx *ctx, const cloak_stack_desc *d, float *
     // workspace: bf16 activations, partial sums, counters, barrier
     const size_t act_elems = (size_t)M * (D + HQ + 2 * HKV + F);
     const size_t part_words = (size_t)G * 2 * 128 * PSTRIDE;  // tagged 64-bit words
-    const size_t partf_floats = npad > 16 ? (size_t)G * 2 * 2 * 128 * npad : 0;
+    const size_t partf_floats = (size_t)G * 2 * 2 * 128 * npad;
     size_t rows = 0;
     for (int l = 0; l < d->num_layers; ++l)
         for (int j = 0; j < 7; ++j) rows += ctx->info[d->layer_tensors[l * 7 + j]].nt;
@@ -919,7 +1054,7 @@ cloak_status stack_decode_run(cloak_ctx *ctx, const cloak_stack_desc *d, float *
     auto r256 = [](size_t n) { return (n + 255) & ~(size_t)255; };
     const size_t bytes = r256((size_t)M * D * 2) + r256((size_t)M * HQ * 2) + 2 * r256((size_t)M * HKV * 2) +
                          r256((size_t)M * F * 2) + r256(part_words * 8) + r256(16) + r256(partf_floats * 4) + r256(rows * 4) +
-                         r256(nstages * sizeof(StackStage)) + r256((size_t)(D / 128 + 1) * 64 * 4);
+                         r256(nstages * sizeof(StackStage)) + r256(((size_t)(D / 128) * 4 + 1) * 64 * 4);
     (void)act_elems;
     cudaError_t err = cudaSuccess;
     void *before = ctx->d_stack_ws;
@@ -947,7 +1082,7 @@ cloak_status stack_decode_run(cloak_ctx *ctx, const cloak_stack_desc *d, float *
     float *partf = (float *)take(partf_floats * 4);
     uint32_t *cnt = (uint32_t *)take(rows * 4);
     StackStage *dst = (StackStage *)take(nstages * sizeof(StackStage));
-    float *ss = (float *)take((size_t)(D / 128 + 1) * 64 * 4);  // [D/128][64] row tiles, then [64] input
+    float *ss = (float *)take(((size_t)(D / 128) * 4 + 1) * 64 * 4);  // [D/128][4][64] quarter tiles, then [64] input
     // the stage program
     std::vector<StackStage> st(nstages);
     size_t roff = 0;
@@ -1004,7 +1139,7 @@ cloak_status stack_decode_run(cloak_ctx *ctx, const cloak_stack_desc *d, float *
     }
     CLOAK_CUDA(ctx, cudaMemsetAsync(cnt, 0, rows * 4, s));
     CLOAK_CUDA(ctx, cudaMemsetAsync(bar, 0, 8, s));
-    k_stack_input<<<M, 256, 0, s>>>(h, D, hb, ss + (size_t)(D / 128) * 64, bar + 2);
+    k_stack_input<<<M, 256, 0, s>>>(h, D, hb, ss + (size_t)(D / 128) * 4 * 64, bar + 2);
     CLOAK_LAUNCHED(ctx);
     StackMaps xm;
     if (!encode_tmap_2d(&xm.m[XMAP_H], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, hb, D, M, (uint64_t)D * 2, 64, npad) ||
@@ -1028,14 +1163,17 @@ cloak_status stack_decode_run(cloak_ctx *ctx, const cloak_stack_desc *d, float *
     a.partf = partf;
     a.epoch = bar + 2;
     a.ss_rows = ss;
-    a.ss_init = ss + (size_t)(D / 128) * 64;
+    a.ss_init = ss + (size_t)(D / 128) * 4 * 64;
     a.bar = bar;
     a.abort = (int *)(bar + 1);
     a.status = ctx->d_status;
     const CUtensorMap &tw = weight_map(ctx, flags);
-    if (npad == 16) return launch_stack<16>(ctx, tw, xm, a, s);
-    if (npad == 32) return launch_stack<32>(ctx, tw, xm, a, s);
-    return launch_stack<64>(ctx, tw, xm, a, s);
+    if (npad == 16) {
+        if (M <= STACK_TAG_MAX_M) return launch_stack<16, true>(ctx, tw, xm, a, s);
+        return launch_stack<16, false>(ctx, tw, xm, a, s);
+    }
+    if (npad == 32) return launch_stack<32, false>(ctx, tw, xm, a, s);
+    return launch_stack<64, false>(ctx, tw, xm, a, s);
 }
 
 }  // namespace cloak

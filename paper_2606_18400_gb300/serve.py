@@ -179,6 +179,7 @@ class Server:
         self._rk = None              # the re-key in flight
         self.steps = 0
         self.step_tokens: List[int] = []
+        self.tokens_out = 0          # sampled tokens, finished requests or not
 
     def _admit(self, r: Request, now: float) -> bool:
         need = -(-(len(r.prompt) + r.max_new) // BLOCK)
@@ -293,6 +294,7 @@ class Server:
                 due = False
             owners, toks = self.step_batch(running, lambda: self._rekey_boundary(due))
             t = time.perf_counter() - t0
+            self.tokens_out += len(toks)
             for r, tok in zip(owners, toks):
                 r.out.append(int(tok))
                 if r.t_first is None:

@@ -67,19 +67,67 @@ def test_full_size_two_layer_stack(cloak_lib, M):
     cm.close()
 
 
-def test_full_stack_32_layers_cloaked_equals_uncloaked(cloak_lib):
-    """The 12.95 GB 32-layer stack (weights drawn on the device): one decode
-    step is finite and bit-identical between the cloaked arena and the twin."""
+def test_full_stack_32_layers_against_the_oracle(cloak_lib):
+    """The 12.95 GB 32-layer stack (weights drawn on the device), decode at
+    M = 1 and M = 8, checked layer by layer against the FP64 oracle: the
+    launch runs the first l layers for every l = 1..32 (the same stage splits
+    as the full stack, so the same intermediate states), and each layer's
+    output must be within 1e-2 of the oracle's layer step applied to the
+    launch's own input of that layer, normwise and per token. Each layer's
+    weights are redrawn on the device from their seeds and brought to the
+    host alone. The full 32-layer step is bit-identical between the cloaked
+    arena and the twin. The drift of the whole step from the all-FP64 chain
+    is printed: this random-weight model amplifies any per-layer difference
+    (its residual stream grows about 15-fold over the 32 layers), so the
+    chain is not a bound on the kernel."""
+    import concurrent.futures as cf
     m = synth.llama7b_layer(32)
+    one = synth.llama7b_layer(1)  # the structure of one layer for the oracle
     cm = cloak_lib.CloakModel(m, twin=True)
     cm.keygen(0x1234, 0)
     for t in range(len(m.tensors)):
         cm.shuffle(t, synth.weights_device(m, t, seed=0))
-    h0 = torch.from_numpy(synth.activations_host(4, 4096, seed=3)).cuda()
-    h1 = cm.stack_decode(h0.clone())
-    h2 = cm.stack_decode(h0.clone(), uncloaked=True)
-    torch.cuda.synchronize()
-    assert torch.isfinite(h1).all()
-    assert torch.equal(h1, h2)
+    desc = cm.stack_desc()
+    lt = [desc.layer_tensors[i] for i in range(32 * 7)]
+    h0 = {M: synth.activations_host(M, 4096, seed=30 + M) for M in (1, 8)}
+    hs = {}
+    for M in (1, 8):
+        hs[M] = [h0[M].astype(np.float64)]
+        for l in range(1, 33):
+            desc.num_layers = l
+            h = cm.stack_decode(torch.from_numpy(h0[M]).cuda(), desc=desc)
+            torch.cuda.synchronize()
+            hs[M].append(h.cpu().numpy().astype(np.float64))
+        h2 = cm.stack_decode(torch.from_numpy(h0[M]).cuda(), uncloaked=True, desc=desc)
+        torch.cuda.synchronize()
+        assert np.array_equal(h2.cpu().numpy().astype(np.float64), hs[M][32])
     assert cm.device_status() == 0
     cm.close()
+    exact = {M: h0[M].astype(np.float64) for M in (1, 8)}
+
+    def w64(t):
+        return O.bf16_value(O.bf16_bits(synth.weights_device(m, t, seed=0).cpu().numpy()))
+
+    worst = {1: 0.0, 8: 0.0}
+    worst_b = {1: 0.0, 8: 0.0}
+    with cf.ThreadPoolExecutor(7) as ex:
+        for l in range(32):
+            W64 = list(ex.map(w64, lt[7 * l:7 * l + 7]))  # q, k, v, o, gate, up, down
+            for M in (1, 8):
+                ref = O.stack_decode_f64(one, W64, hs[M][l])
+                err = O.relative_error(hs[M][l + 1], ref)
+                assert err <= 1e-2, (M, l, err)
+                for i in range(M):
+                    assert O.relative_error(hs[M][l + 1][i:i + 1], ref[i:i + 1]) <= 1e-2, (M, l, i)
+                worst[M] = max(worst[M], err)
+                refb = O.stack_decode_f64(one, W64, hs[M][l], bf16_operands=True)
+                worst_b[M] = max(worst_b[M], O.relative_error(hs[M][l + 1], refb))
+                exact[M] = O.stack_decode_f64(one, W64, exact[M])
+            del W64
+    for M in (1, 8):
+        drift = O.relative_error(hs[M][32], exact[M])
+        grow = O.relative_error(exact[M], h0[M].astype(np.float64))
+        print(f"32-layer stack M={M}: worst layer {worst[M]:.3e} vs the FP64 step, "
+              f"{worst_b[M]:.3e} vs the BF16-operand step; whole step {drift:.3e} from the "
+              f"all-FP64 chain (residual change {grow:.1f}x)")
+        assert grow > 0.5
