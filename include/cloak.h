@@ -108,11 +108,13 @@ enum {
                               draws): cloak_rekey then moves every tile
                               (32 KiB BF16, 16 KiB E4M3) to its slot under the
                               new tables, so tiles also change pages and
-                              neighbours: through a temporary device buffer
-                              of the arena's size while the call runs (in
-                              place through the staging pages if it cannot
-                              be allocated, or if the environment sets
-                              CLOAK_TILE_REKEY_IN_PLACE=1). Synchronous
+                              neighbours: through a device buffer of the
+                              arena's size, allocated by the first such
+                              re-key and kept by the context until
+                              cloak_destroy (in place through the staging
+                              pages if it cannot be allocated, or if the
+                              environment sets CLOAK_TILE_REKEY_IN_PLACE=1);
+                              the arena keeps its address. Synchronous
                               re-keys only:
                               cloak_rekey_begin returns CLOAK_E_UNSUPPORTED. */
 };

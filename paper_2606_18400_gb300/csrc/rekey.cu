@@ -569,16 +569,30 @@ __global__ void k_zero_tail_slots(const uint32_t *page_alloc, uint32_t G, uint32
 }
 
 // Out-of-place tile moves: tile g from its old slot in the arena to its new
-// slot in `tmp` (an arena-sized buffer); 16-byte loads and stores, one tile
-// per block iteration.
-__global__ void __launch_bounds__(256) k_tile_gather(const uint32_t *old_slot, const uint32_t *new_slot,
-                                                     uint32_t G, const uint8_t *arena, uint8_t *tmp,
+// slot in `tmp` (an arena-sized buffer); one tile per block iteration, each
+// thread's 16-byte loads of the tile all in flight before its stores.
+__global__ void __launch_bounds__(256) k_tile_gather(const uint32_t *__restrict__ old_slot,
+                                                     const uint32_t *__restrict__ new_slot, uint32_t G,
+                                                     const uint8_t *__restrict__ arena, uint8_t *__restrict__ tmp,
                                                      int64_t tile_bytes) {
+    constexpr int PT = 8;  // 16-byte pieces per thread and round: 32 KiB per block round
     const int64_t n16 = tile_bytes / 16;
     for (uint32_t g = blockIdx.x; g < G; g += gridDim.x) {
         const uint4 *src = reinterpret_cast<const uint4 *>(arena + (int64_t)old_slot[g] * tile_bytes);
         uint4 *dst = reinterpret_cast<uint4 *>(tmp + (int64_t)new_slot[g] * tile_bytes);
-        for (int64_t i = threadIdx.x; i < n16; i += blockDim.x) __stcs(dst + i, __ldcs(src + i));
+        for (int64_t i0 = 0; i0 < n16; i0 += (int64_t)PT * blockDim.x) {
+            uint4 v[PT];
+#pragma unroll
+            for (int j = 0; j < PT; ++j) {
+                const int64_t i = i0 + (int64_t)j * blockDim.x + threadIdx.x;
+                if (i < n16) v[j] = __ldcs(src + i);
+            }
+#pragma unroll
+            for (int j = 0; j < PT; ++j) {
+                const int64_t i = i0 + (int64_t)j * blockDim.x + threadIdx.x;
+                if (i < n16) __stcs(dst + i, v[j]);
+            }
+        }
     }
 }
 
@@ -600,24 +614,26 @@ cloak_status tile_rekey_run(cloak_ctx *ctx, uint64_t key, uint32_t new_epoch, cu
         return rc;
     }
     // Out of place when an arena-sized buffer can be had (HBM is large next
-    // to most models): every tile to its new slot in the buffer, then one
-    // device copy back. Else in place, through the planner and the staging
+    // to most models; the first such re-key allocates it and the context
+    // keeps it): every tile to its new slot in the buffer, then one device
+    // copy back (the arena keeps its address, so tensor maps and captured
+    // graphs stay valid). Else in place, through the planner and the staging
     // pages, like the page re-key.
     const size_t bytes = (size_t)ctx->NPS * (size_t)ctx->page_bytes;
     const char *ip = getenv("CLOAK_TILE_REKEY_IN_PLACE");  // no temporary buffer wanted
     const bool in_place = ip && ip[0] == '1';
-    uint8_t *tmp = nullptr;
-    if (!in_place && cudaMallocAsync((void **)&tmp, bytes, s) == cudaSuccess) {
+    if (!in_place && !ctx->d_tile_tmp && cudaMalloc((void **)&ctx->d_tile_tmp, bytes) != cudaSuccess) {
+        ctx->d_tile_tmp = nullptr;
+        cudaGetLastError();  // the failed allocation is not a sticky error
+    }
+    if (!in_place && ctx->d_tile_tmp) {
         k_tile_gather<<<ctx->sm_count * 8, 256, 0, s>>>(ctx->d_slot_old, ctx->d_tile_slot, (uint32_t)ctx->G,
-                                                        ctx->arena, tmp, ctx->tile_bytes);
+                                                        ctx->arena, ctx->d_tile_tmp, ctx->tile_bytes);
         ctx->launches++;
         cudaError_t e = cudaGetLastError();
-        if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->arena, tmp, bytes, cudaMemcpyDeviceToDevice, s);
-        const cudaError_t ef = cudaFreeAsync(tmp, s);  // released on every path
-        if (e == cudaSuccess) e = ef;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->arena, ctx->d_tile_tmp, bytes, cudaMemcpyDeviceToDevice, s);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "tile re-key (out of place)");
     } else {
-        if (!in_place) cudaGetLastError();  // the failed allocation is not a sticky error
         const MoveSet m{ctx->d_slot_old, ctx->d_tile_slot, (uint32_t)ctx->G, (uint32_t)(ctx->NPS * ctx->tpp),
                         (uint32_t)(ctx->stage_pages * ctx->tpp), ctx->tile_bytes};
         std::vector<uint32_t> ws;
