@@ -19,8 +19,11 @@
 // whole 128x128 E4M3 tile. The same code serves both types; E4M3 applies the
 // per-row weight scale and per-token activation scale in the epilogue.
 //
-// Warp roles (192 threads): warp 0 TMA (gather-table entries fetched 32 k-tiles
-// ahead by the whole warp), warp 1 TMEM owner + MMA issue, warps 2-5 epilogue.
+// Warp roles (320 threads): warp 0 TMA (gather-table entries fetched 32 k-tiles
+// ahead by the whole warp), warp 1 TMEM owner + MMA issue, warps 2-9 epilogue:
+// two warps per TMEM lane quarter, each draining half of every 32 tokens (the
+// drain is instruction-bound: one warp per scheduler left the tensor cores
+// idle for a third of the launch while it ran).
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -32,6 +35,7 @@
 namespace cloak {
 
 constexpr int GMAXP = 8;
+constexpr int GEPI = 256;  // epilogue threads (warps 2-9)
 
 struct GemmProblem {
     uint32_t base;         // first logical tile of the tensor
@@ -61,7 +65,7 @@ struct GemmCfg {
     static constexpr int B_BYTES = 256 * 128;     // 256 tokens x 128 bytes
     static constexpr int STAGE = 2 * A_HALF + B_BYTES;
     static constexpr int STAGES = 3;
-    static constexpr int SMEM = STAGES * STAGE + 1024 + 1024;
+    static constexpr int SMEM = STAGES * STAGE + 1024 + 1024 + 2048;  // + two tiles' activation scales
     static constexpr int QD = 4;                  // depth of the tile-index queue
     static constexpr uint32_t IDESC = idesc_make(FP8 ? 0u : 1u, 128, 256);
 };
@@ -93,7 +97,7 @@ __device__ __forceinline__ uint32_t gslot(const GemmArgs &g, const GemmProblem &
 }
 
 template <bool FP8>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(64 + GEPI, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tw, const __grid_constant__ GemmMaps xm,
               const __grid_constant__ GemmArgs g) {
     using C = GemmCfg<FP8>;
@@ -108,6 +112,7 @@ __global__ void __launch_bounds__(192, 1)
     uint64_t *id_empty = id_full + C::QD;  // [QD] the MMA thread and all epilogue threads read it
     uint32_t *ids = reinterpret_cast<uint32_t *>(id_empty + C::QD);
     uint32_t *tmem_slot = ids + C::QD;
+    float *xs_smem = reinterpret_cast<float *>(smem + C::STAGES * C::STAGE + 1024);  // [2][256]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -116,10 +121,10 @@ __global__ void __launch_bounds__(192, 1)
             mbar_init(&empty[s], 1);
         }
         mbar_init(tfull, 1);
-        mbar_init(tempty, 128);
+        mbar_init(tempty, GEPI);
         for (int q = 0; q < C::QD; ++q) {
             mbar_init(&id_full[q], 1);
-            mbar_init(&id_empty[q], 129);
+            mbar_init(&id_empty[q], 1 + GEPI);
         }
         fence_mbar_init();
         prefetch_tmap(&tw);
@@ -227,8 +232,10 @@ __global__ void __launch_bounds__(192, 1)
         }
     } else {
         // ---------------------------------------------------------- epilogue
-        const int qd = warp & 3;
+        const int qd = warp & 3;               // TMEM lane quarter of this warp
         const int r_in = qd * 32 + lane;
+        const int th = (warp >= 6) ? 16 : 0;   // which 16 of every 32 tokens
+        const int et = threadIdx.x - 64;
         for (uint32_t n = 0;; ++n) {
             const int q = n % C::QD;
             if (!mbar_wait(&id_full[q], (n / C::QD) & 1, g.status)) break;
@@ -238,39 +245,67 @@ __global__ void __launch_bounds__(192, 1)
             const GItem w = gitem(g, item);
             const GemmProblem &P = g.p[w.p];
             float wsc[2] = {1.0f, 1.0f};
+            float *xs = xs_smem + (n & 1) * 256;  // the tile's activation scales (E4M3)
             if (FP8) {
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const int row = w.rp * 256 + h * 128 + r_in;
                     wsc[h] = row < P.N ? P.w_scale[row] : 0.0f;
                 }
+                // two buffers by tile parity: the one written here was last read
+                // two tiles ago, before the barrier below of the previous tile
+                if (et < 256) {
+                    const int m = w.tc * 256 + et;
+                    xs[et] = m < g.M ? P.x_scale[m] : 0.0f;
+                }
+                asm volatile("bar.sync 1, %0;" ::"n"(GEPI) : "memory");
             }
+            const int N = P.N;
+            const int nh = w.two ? 2 : 1;
             if (!mbar_wait(tfull, n & 1, g.status)) break;
             tc_fence_after();
             const uint32_t taddr = tmem + ((uint32_t)(qd * 32) << 16);
+            // per round, this warp's 16 tokens of both row halves: two TMEM
+            // loads, one wait; then 16 outputs per row along a running pointer
 #pragma unroll 1
-            for (int c0 = 0; c0 < 256; c0 += 16) {
+            for (int c0 = th; c0 < 256; c0 += 32) {
                 const int m0 = w.tc * 256 + c0;
                 if (m0 >= g.M) break;
-                float xsc[16];
+                const int nt = min(16, g.M - m0);
+                uint32_t v[2][16];
+                tmem_ld16_nw(taddr + c0, v[0]);
+                if (nh == 2) tmem_ld16_nw(taddr + 256 + c0, v[1]);
+                tmem_wait_ld(v[0]);
+                if (nh == 2) tmem_hold(v[1]);
+                float sx[16];
 #pragma unroll
-                for (int j = 0; j < 16; ++j) xsc[j] = (FP8 && m0 + j < g.M) ? P.x_scale[m0 + j] : 1.0f;
+                for (int j = 0; j < 16; ++j) sx[j] = FP8 ? xs[c0 + j] : 1.0f;
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    if (h == 1 && !w.two) break;
+                    if (h >= nh) break;
                     const int row = w.rp * 256 + h * 128 + r_in;
-                    float v[16];
-                    tmem_ld16(taddr + h * 256 + c0, v);
-                    if (row >= P.N) continue;
+                    if (row >= N) continue;
+                    float o[16];
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
-                        const int m = m0 + j;
-                        if (m >= g.M) break;
-                        float o = v[j];
-                        if (FP8) o = o * wsc[h] * xsc[j];
-                        if (g.relu) o = fmaxf(o, 0.0f);
-                        if (g.out_f32) reinterpret_cast<float *>(P.y)[(int64_t)m * P.N + row] = o;
-                        else reinterpret_cast<__nv_bfloat16 *>(P.y)[(int64_t)m * P.N + row] = __float2bfloat16_rn(o);
+                        o[j] = __uint_as_float(v[h][j]);
+                        if (FP8) o[j] *= wsc[h] * sx[j];
+                        if (g.relu) o[j] = fmaxf(o[j], 0.0f);
+                    }
+                    if (g.out_f32) {
+                        float *py = reinterpret_cast<float *>(P.y) + (int64_t)m0 * N + row;
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            if (j < nt) *py = o[j];
+                            py += N;
+                        }
+                    } else {
+                        __nv_bfloat16 *py = reinterpret_cast<__nv_bfloat16 *>(P.y) + (int64_t)m0 * N + row;
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            if (j < nt) *py = __float2bfloat16_rn(o[j]);
+                            py += N;
+                        }
                     }
                 }
             }
@@ -295,7 +330,7 @@ static cloak_status gemm_launch(cloak_ctx *ctx, const CUtensorMap &tw, const Gem
         CLOAK_CUDA(ctx, cudaFuncSetAttribute(k_gemm_tc<FP8>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
         attr_set_on(attr_devs, ctx->device);
     }
-    k_gemm_tc<FP8><<<grid, 192, C::SMEM, s>>>(tw, mp, g);
+    k_gemm_tc<FP8><<<grid, 64 + GEPI, C::SMEM, s>>>(tw, mp, g);
     CLOAK_LAUNCHED(ctx);
     return CLOAK_OK;
 }
