@@ -145,6 +145,8 @@ struct cloak_ctx {
     int stack_l2_pf_force = -1;                // set while the tuner measures the stack kernel
     void *d_serve_ws = nullptr;                // serving-step workspace
     size_t serve_ws_cap = 0;
+    uint32_t *d_att_cnt = nullptr;             // decode attention: split arrivals per (token, head),
+    size_t att_cnt_cap = 0;                    // zero between launches (the last arriver resets)
     void *d_moe_ws = nullptr;                  // MoE FFN workspace (expert table first)
     size_t moe_ws_cap = 0;
     std::vector<uint32_t> moe_tab;             // expert table last uploaded
@@ -153,6 +155,8 @@ struct cloak_ctx {
     std::unordered_map<std::string, cloak::TuneCfg> tune;
     const cloak::TuneCfg *tune_force = nullptr;  // set while the tuner measures
     bool tune_invariant = false;                 // keep the default CTA split (serving)
+    bool chained = false;                        // launches follow this library's own kernels on the
+                                                 // stream: programmatic dependent launches
 
     bool keyed = false, placed_any = false;
     uint64_t key = 0;
@@ -176,6 +180,27 @@ cloak_status cuda_fail(cloak_ctx *ctx, cudaError_t e, const char *where);
         cudaError_t e_ = cudaGetLastError();                            \
         if (e_ != cudaSuccess) return cloak::cuda_fail(ctx, e_, "launch"); \
     } while (0)
+
+// A launch that may be programmatically dependent on the stream's previous
+// kernel (`chained`): it may start while that kernel finishes, so it must
+// execute griddepcontrol.wait before it reads anything an earlier kernel
+// wrote, and before it exits (the wait is what orders the chain's
+// completions). Without `chained` it is an ordinary launch.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k(bool chained, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                            cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = grid;
+    lc.blockDim = block;
+    lc.dynamicSmemBytes = smem;
+    lc.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    lc.attrs = attr;
+    lc.numAttrs = chained ? 1 : 0;
+    return cudaLaunchKernelEx(&lc, kern, args...);
+}
 
 bool encode_tmap_2d(CUtensorMap *map, CUtensorMapDataType dt, const void *base, uint64_t inner,
                     uint64_t outer, uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer);

@@ -301,6 +301,9 @@ __global__ void __launch_bounds__(192, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint64_t T = b.total, G = gridDim.x;
     const uint64_t u0 = blockIdx.x * T / G, u1 = (blockIdx.x + 1) * T / G;
+    // a dependent launch of the next kernel may start as SMs free up; it
+    // waits for this grid's completion before it reads what this one writes
+    griddep_launch_dependents();
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < NS; ++s) {
@@ -678,21 +681,9 @@ static cloak_status launch_tc(cloak_ctx *ctx, const CUtensorMap &tw, const void 
         ctx->part_cap = need;
     }
     b.part = ctx->d_part;
-    if (b.dep_wait) {
-        cudaLaunchConfig_t lc = {};
-        lc.gridDim = dim3(grid);
-        lc.blockDim = dim3(192);
-        lc.dynamicSmemBytes = smem;
-        lc.stream = s;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-        attr[0].val.programmaticStreamSerializationAllowed = 1;
-        lc.attrs = attr;
-        lc.numAttrs = 1;
-        CLOAK_CUDA(ctx, cudaLaunchKernelEx(&lc, k_linear_tc<FP8, NPAD>, tw, tx, b));
-    } else {
-        k_linear_tc<FP8, NPAD><<<grid, 192, smem, s>>>(tw, tx, b);
-    }
+    // after this library's own kernels the weight ring fills while they finish
+    if (ctx->chained) b.dep_wait = 1;
+    CLOAK_CUDA(ctx, launch_k(b.dep_wait != 0, k_linear_tc<FP8, NPAD>, dim3(grid), dim3(192), smem, s, tw, tx, b));
     CLOAK_LAUNCHED(ctx);
     return CLOAK_OK;
 }

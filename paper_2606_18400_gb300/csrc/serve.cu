@@ -19,8 +19,18 @@
 #include <cmath>
 
 #include "internal.cuh"
+#include "ptx.cuh"
 
 namespace cloak {
+
+// Every kernel of a step: the next kernel may be scheduled at once (it waits
+// for this one's completion before it reads this one's outputs), and this one
+// waits for the previous kernel's completion before it reads anything.
+// Without a programmatic dependent launch both are no-ops.
+__device__ __forceinline__ void chain_enter() {
+    griddep_launch_dependents();
+    griddep_wait();
+}
 
 static inline unsigned nb(size_t n, unsigned b = 256) { return (unsigned)((n + b - 1) / b); }
 
@@ -49,6 +59,7 @@ static cloak_status step_linears(cloak_ctx *ctx, int n, const int32_t *ts, const
 
 // token ids outside [0, V) give a zero row
 __global__ void k_embed(const __nv_bfloat16 *emb, const int32_t *ids, int D, int V, float *h) {
+    chain_enter();
     const int m = blockIdx.x;
     const int id = ids[m];
     if ((unsigned)id >= (unsigned)V) {
@@ -65,6 +76,7 @@ __global__ void k_embed(const __nv_bfloat16 *emb, const int32_t *ids, int D, int
 // slot g); 16-byte loads of 8 BF16 columns.
 __global__ void k_embed_tiled(const uint8_t *wbase, const uint32_t *slot_of, uint32_t base, int kt,
                               const int32_t *ids, int D, int V, float *h) {
+    chain_enter();
     const int m = blockIdx.x;
     const int id = ids[m];
     if ((unsigned)id >= (unsigned)V) {
@@ -90,6 +102,7 @@ __global__ void k_embed_tiled(const uint8_t *wbase, const uint32_t *slot_of, uin
 
 // x = bf16(h * r), r = 1/sqrt(mean(h^2) + eps); optional row subset
 __global__ void k_rmsnorm(const float *h, const int32_t *rows, int D, float eps, __nv_bfloat16 *x) {
+    chain_enter();
     const int m = blockIdx.x;
     const int src = rows ? rows[m] : m;
     const float *hr = h + (size_t)src * D;
@@ -109,12 +122,72 @@ __global__ void k_rmsnorm(const float *h, const int32_t *rows, int D, float eps,
     for (int c = threadIdx.x; c < D; c += blockDim.x) x[(size_t)m * D + c] = __float2bfloat16_rn(hr[c] * r);
 }
 
+// Residual add and RMSNorm in one pass over a token's row: h += y (y may be
+// null), then x = bf16(h * r), r = 1/sqrt(mean(h^2) + eps). Block i takes
+// token rows[i] (rows null: token i) and writes x row i. 16-byte loads; the
+// row (d_model a multiple of 4, at most 256 * 4 * VR) stays in registers.
+// The sum of squares: each thread's own values in column order, then a
+// fixed tree over the lanes and the warps, so a token's result does not
+// depend on the batch.
+template <int VR>
+__global__ void __launch_bounds__(256) k_add_rmsnorm(float *h, const float *y, const int32_t *rows, int D,
+                                                     float eps, __nv_bfloat16 *x) {
+    chain_enter();
+    const int i = blockIdx.x, t = threadIdx.x;
+    const int src = rows ? rows[i] : i;
+    float4 *hr = reinterpret_cast<float4 *>(h + (size_t)src * D);
+    const float4 *yr = y ? reinterpret_cast<const float4 *>(y + (size_t)src * D) : nullptr;
+    const int D4 = D / 4;
+    float4 v[VR];
+#pragma unroll
+    for (int k = 0; k < VR; ++k) {
+        const int c = k * 256 + t;
+        v[k] = c < D4 ? hr[c] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
+    if (yr) {
+#pragma unroll
+        for (int k = 0; k < VR; ++k) {
+            const int c = k * 256 + t;
+            if (c < D4) {
+                const float4 a = yr[c];
+                v[k].x += a.x;
+                v[k].y += a.y;
+                v[k].z += a.z;
+                v[k].w += a.w;
+                hr[c] = v[k];
+            }
+        }
+    }
+    float ss = 0.0f;
+#pragma unroll
+    for (int k = 0; k < VR; ++k)
+        ss = fmaf(v[k].w, v[k].w, fmaf(v[k].z, v[k].z, fmaf(v[k].y, v[k].y, fmaf(v[k].x, v[k].x, ss))));
+    __shared__ float red[8];
+    for (int o = 16; o; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    if ((t & 31) == 0) red[t >> 5] = ss;
+    __syncthreads();
+    ss = ((red[0] + red[1]) + (red[2] + red[3])) + ((red[4] + red[5]) + (red[6] + red[7]));
+    const float r = rsqrtf(ss / (float)D + eps);
+    uint2 *xr = reinterpret_cast<uint2 *>(x + (size_t)i * D);
+#pragma unroll
+    for (int k = 0; k < VR; ++k) {
+        const int c = k * 256 + t;
+        if (c < D4) {
+            const __nv_bfloat162 lo = __floats2bfloat162_rn(v[k].x * r, v[k].y * r);
+            const __nv_bfloat162 hi = __floats2bfloat162_rn(v[k].z * r, v[k].w * r);
+            xr[c] = make_uint2(*reinterpret_cast<const uint32_t *>(&lo), *reinterpret_cast<const uint32_t *>(&hi));
+        }
+    }
+}
+constexpr int NORM_VR = 8;  // d_model up to 8192 in registers
+
 // RoPE (rotate-half pairs (i, i+64) of a 128-dim head, angle pos * theta^(-i/64))
 // on q and k; k and v written to the paged cache [block][16][n_kv][128].
 __global__ void k_rope_cache(__nv_bfloat16 *q, const __nv_bfloat16 *k, const __nv_bfloat16 *v,
                              const int32_t *pos, const int32_t *req, const int32_t *btab,
                              int max_blocks, int HQ, int HKV, float theta, __nv_bfloat16 *kc,
                              __nv_bfloat16 *vc) {
+    chain_enter();
     const int m = blockIdx.x, head = blockIdx.y, i = threadIdx.x;  // i < 64
     const int p = pos[m];
     const float freq = powf(theta, -(float)i / 64.0f);
@@ -140,30 +213,32 @@ __global__ void k_rope_cache(__nv_bfloat16 *q, const __nv_bfloat16 *k, const __n
 }
 
 // Causal attention of single queries (decode tokens), split over the keys:
-// block (split, row, head) takes keys [256 split, 256 split + 256) of token
-// m = rows[row]; each of its 4 warps 64 of them, 8 at a time. A lane holds 4
+// block (split, row, head) takes keys [64 split, 64 split + 64) of token
+// m = rows[row]; each of its 4 warps 16 of them, 8 at a time. A lane holds 4
 // of the 128 dimensions: K and V rows are read as 256-byte coalesced warp
 // loads, 16 of them in flight per lane; scores are warp sums. Online softmax
 // in FP32 per warp, merged across the warps in shared memory. A token with
 // one split writes its output; otherwise the block writes (max, sum,
-// acc[128]) and k_attn_combine merges the splits in order. The split depends
-// only on the token's own position, so the result does not depend on the
-// batch.
-constexpr int ATT_SPLIT = 256;
+// acc[128]) and the last of the token's blocks to finish (an arrival count
+// per token and head) merges the splits in order. The split depends only on
+// the token's own position, so the result does not depend on the batch.
+constexpr int ATT_SPLIT = 64;
 constexpr int ATT_PART = 132;  // floats per partial: max, sum, pad, acc[128]
+constexpr int ATT_GRID_X = 16;  // blocks per (token, head); longer contexts loop
 
 __global__ void __launch_bounds__(128) k_attn_decode(const __nv_bfloat16 *q, const __nv_bfloat16 *kc,
                                                      const __nv_bfloat16 *vc, const int32_t *pos,
                                                      const int32_t *req, const int32_t *btab,
                                                      const int32_t *rows, int max_blocks, int HQ,
                                                      int HKV, int max_splits, float *part,
-                                                     __nv_bfloat16 *out) {
-    const int sp = blockIdx.x, r = blockIdx.y, j = blockIdx.z;
+                                                     uint32_t *cnt, __nv_bfloat16 *out) {
+    chain_enter();
+    const int r = blockIdx.y, j = blockIdx.z;
     const int m = rows ? rows[r] : r;
     const int n = pos[m] + 1;
     const int nsplit = (n + ATT_SPLIT - 1) / ATT_SPLIT;
-    if (sp >= nsplit) return;
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if ((int)blockIdx.x >= nsplit) return;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, t = threadIdx.x;
     const int kvh = j / (HQ / HKV);
     const int32_t *bt = btab + (size_t)req[m] * max_blocks;
     float qd[4];
@@ -174,101 +249,106 @@ __global__ void __launch_bounds__(128) k_attn_decode(const __nv_bfloat16 *q, con
         const float sc = 0.08838834764831845f;  // 1/sqrt(128)
         qd[0] = a.x * sc; qd[1] = a.y * sc; qd[2] = b.x * sc; qd[3] = b.y * sc;
     }
-    const int k_begin = sp * ATT_SPLIT + w * (ATT_SPLIT / 4);
-    const int k_end = min(n, k_begin + ATT_SPLIT / 4);
-    float mx = -FLT_MAX, sum = 0.0f, acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    for (int kb = k_begin; kb < k_end; kb += 8) {
-        uint2 kr[8], vr[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int key = min(kb + i, k_end - 1);
-            const size_t off = (((size_t)bt[key >> 4] * 16 + (key & 15)) * HKV + kvh) * 128 + 4 * lane;
-            kr[i] = *reinterpret_cast<const uint2 *>(kc + off);
-            vr[i] = *reinterpret_cast<const uint2 *>(vc + off);
-        }
-        float s[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const __nv_bfloat162 *h2 = reinterpret_cast<const __nv_bfloat162 *>(&kr[i]);
-            const float2 a = __bfloat1622float2(h2[0]), b = __bfloat1622float2(h2[1]);
-            s[i] = fmaf(qd[0], a.x, fmaf(qd[1], a.y, fmaf(qd[2], b.x, qd[3] * b.y)));
-        }
-#pragma unroll
-        for (int o = 16; o; o >>= 1) {
-#pragma unroll
-            for (int i = 0; i < 8; ++i) s[i] += __shfl_xor_sync(0xffffffffu, s[i], o);
-        }
-        float cm = mx;
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            if (kb + i >= k_end) s[i] = -FLT_MAX;
-            cm = fmaxf(cm, s[i]);
-        }
-        const float scale = expf(mx - cm);
-        sum *= scale;
-#pragma unroll
-        for (int d = 0; d < 4; ++d) acc[d] *= scale;
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const float p = kb + i < k_end ? expf(s[i] - cm) : 0.0f;
-            sum += p;
-            const __nv_bfloat162 *h2 = reinterpret_cast<const __nv_bfloat162 *>(&vr[i]);
-            const float2 a = __bfloat1622float2(h2[0]), b = __bfloat1622float2(h2[1]);
-            acc[0] = fmaf(p, a.x, acc[0]);
-            acc[1] = fmaf(p, a.y, acc[1]);
-            acc[2] = fmaf(p, b.x, acc[2]);
-            acc[3] = fmaf(p, b.y, acc[3]);
-        }
-        mx = cm;
-    }
-    // merge the four warps
     __shared__ float wm[4], wl[4];
     __shared__ float wa[4][128];
-    if (lane == 0) { wm[w] = mx; wl[w] = sum; }
+    __shared__ int last;
+    float *pb = part + ((size_t)r * HQ + j) * max_splits * ATT_PART;
+    // a block takes splits blockIdx.x, blockIdx.x + gridDim.x, ...; each
+    // split's arithmetic is the same whichever block takes it
+    for (int sp = blockIdx.x; sp < nsplit; sp += gridDim.x) {
+        const int k_begin = sp * ATT_SPLIT + w * (ATT_SPLIT / 4);
+        const int k_end = min(n, k_begin + ATT_SPLIT / 4);
+        float mx = -FLT_MAX, sum = 0.0f, acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        for (int kb = k_begin; kb < k_end; kb += 8) {
+            uint2 kr[8], vr[8];
 #pragma unroll
-    for (int d = 0; d < 4; ++d) wa[w][4 * lane + d] = acc[d];
-    __syncthreads();
-    const int t = threadIdx.x;
-    float M = -FLT_MAX;
+            for (int i = 0; i < 8; ++i) {
+                const int key = min(kb + i, k_end - 1);
+                const size_t off = (((size_t)bt[key >> 4] * 16 + (key & 15)) * HKV + kvh) * 128 + 4 * lane;
+                kr[i] = *reinterpret_cast<const uint2 *>(kc + off);
+                vr[i] = *reinterpret_cast<const uint2 *>(vc + off);
+            }
+            float s[8];
 #pragma unroll
-    for (int v = 0; v < 4; ++v)
-        if (wl[v] > 0.0f) M = fmaxf(M, wm[v]);
-    float L = 0.0f, A = 0.0f;
+            for (int i = 0; i < 8; ++i) {
+                const __nv_bfloat162 *h2 = reinterpret_cast<const __nv_bfloat162 *>(&kr[i]);
+                const float2 a = __bfloat1622float2(h2[0]), b = __bfloat1622float2(h2[1]);
+                s[i] = fmaf(qd[0], a.x, fmaf(qd[1], a.y, fmaf(qd[2], b.x, qd[3] * b.y)));
+            }
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
-        if (wl[v] > 0.0f) {
-            const float e = expf(wm[v] - M);
-            L = fmaf(wl[v], e, L);
-            A = fmaf(wa[v][t], e, A);
+            for (int o = 16; o; o >>= 1) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) s[i] += __shfl_xor_sync(0xffffffffu, s[i], o);
+            }
+            float cm = mx;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                if (kb + i >= k_end) s[i] = -FLT_MAX;
+                cm = fmaxf(cm, s[i]);
+            }
+            const float scale = expf(mx - cm);
+            sum *= scale;
+#pragma unroll
+            for (int d = 0; d < 4; ++d) acc[d] *= scale;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const float p = kb + i < k_end ? expf(s[i] - cm) : 0.0f;
+                sum += p;
+                const __nv_bfloat162 *h2 = reinterpret_cast<const __nv_bfloat162 *>(&vr[i]);
+                const float2 a = __bfloat1622float2(h2[0]), b = __bfloat1622float2(h2[1]);
+                acc[0] = fmaf(p, a.x, acc[0]);
+                acc[1] = fmaf(p, a.y, acc[1]);
+                acc[2] = fmaf(p, b.x, acc[2]);
+                acc[3] = fmaf(p, b.y, acc[3]);
+            }
+            mx = cm;
         }
+        // merge the four warps
+        if (lane == 0) { wm[w] = mx; wl[w] = sum; }
+#pragma unroll
+        for (int d = 0; d < 4; ++d) wa[w][4 * lane + d] = acc[d];
+        __syncthreads();
+        float M = -FLT_MAX;
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+            if (wl[v] > 0.0f) M = fmaxf(M, wm[v]);
+        float L = 0.0f, A = 0.0f;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            if (wl[v] > 0.0f) {
+                const float e = expf(wm[v] - M);
+                L = fmaf(wl[v], e, L);
+                A = fmaf(wa[v][t], e, A);
+            }
+        }
+        if (nsplit == 1) {
+            out[((size_t)m * HQ + j) * 128 + t] = __float2bfloat16_rn(A / L);
+            return;
+        }
+        float *pp = pb + sp * ATT_PART;
+        if (t == 0) { pp[0] = M; pp[1] = L; }
+        pp[4 + t] = A;
+        // the last split of (token, head) to finish merges all of them, in
+        // split order (the same arithmetic whichever block it is), and resets
+        // the count; its arrival is the block's last (every split has arrived)
+        __threadfence();
+        __syncthreads();  // also: wm, wl, wa are free for the next split
+        if (t == 0) last = atomicAdd(cnt + (size_t)r * HQ + j, 1u) == (uint32_t)nsplit - 1;
+        __syncthreads();
+        if (last) break;
     }
-    if (nsplit == 1) {
-        out[((size_t)m * HQ + j) * 128 + t] = __float2bfloat16_rn(A / L);
-        return;
+    if (nsplit == 1 || !last) return;
+    __threadfence();
+    float Mx = -FLT_MAX;
+    for (int q = 0; q < nsplit; ++q) Mx = fmaxf(Mx, __ldcg(pb + q * ATT_PART));
+    float Ls = 0.0f, As = 0.0f;
+    for (int q = 0; q < nsplit; ++q) {
+        const float e = expf(__ldcg(pb + q * ATT_PART) - Mx);
+        Ls = fmaf(__ldcg(pb + q * ATT_PART + 1), e, Ls);
+        As = fmaf(__ldcg(pb + q * ATT_PART + 4 + t), e, As);
     }
-    float *pp = part + (((size_t)r * HQ + j) * max_splits + sp) * ATT_PART;
-    if (t == 0) { pp[0] = M; pp[1] = L; }
-    pp[4 + t] = A;
-}
-
-// Merge the splits of tokens with more than one, in split order.
-__global__ void __launch_bounds__(128) k_attn_combine(const int32_t *pos, const int32_t *rows, int HQ,
-                                                      int max_splits, const float *part,
-                                                      __nv_bfloat16 *out) {
-    const int r = blockIdx.x, j = blockIdx.y, t = threadIdx.x;
-    const int m = rows ? rows[r] : r;
-    const int nsplit = (pos[m] + ATT_SPLIT) / ATT_SPLIT;
-    if (nsplit == 1) return;
-    const float *pp = part + ((size_t)r * HQ + j) * max_splits * ATT_PART;
-    float M = -FLT_MAX;
-    for (int sp = 0; sp < nsplit; ++sp) M = fmaxf(M, pp[sp * ATT_PART]);
-    float L = 0.0f, A = 0.0f;
-    for (int sp = 0; sp < nsplit; ++sp) {
-        const float e = expf(pp[sp * ATT_PART] - M);
-        L = fmaf(pp[sp * ATT_PART + 1], e, L);
-        A = fmaf(pp[sp * ATT_PART + 4 + t], e, A);
-    }
-    out[((size_t)m * HQ + j) * 128 + t] = __float2bfloat16_rn(A / L);
+    out[((size_t)m * HQ + j) * 128 + t] = __float2bfloat16_rn(As / Ls);
+    if (t == 0) cnt[(size_t)r * HQ + j] = 0u;
 }
 
 // Query-tiled causal attention for runs of consecutive tokens of one request
@@ -320,6 +400,7 @@ __global__ void __launch_bounds__(128) k_attention_tiled(const __nv_bfloat16 *q,
                                                          const int32_t *req, const int32_t *btab,
                                                          const int32_t *tiles, int max_blocks, int HQ,
                                                          int HKV, __nv_bfloat16 *out) {
+    chain_enter();
     extern __shared__ __align__(128) uint8_t att_smem[];  // [2 buffers][K tile, V tile]
     const int tile = blockIdx.x, j = blockIdx.y, t = threadIdx.x;
     const int warp = t >> 5, lane = t & 31;
@@ -480,11 +561,13 @@ __global__ void __launch_bounds__(128) k_attention_tiled(const __nv_bfloat16 *q,
 }
 
 __global__ void k_add(float *h, const float *y, size_t n) {
+    chain_enter();
     const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (i < n) h[i] += y[i];
 }
 
 __global__ void k_silu_mul(const float *g, const float *u, __nv_bfloat16 *act, size_t n) {
+    chain_enter();
     const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (i < n) {
         const float a = g[i];
@@ -492,14 +575,28 @@ __global__ void k_silu_mul(const float *g, const float *u, __nv_bfloat16 *act, s
     }
 }
 
-// greedy sampling: first index of the maximum logit
-__global__ void k_argmax(const float *logits, int V, int32_t *out) {
+// greedy sampling: first index of the maximum logit (NaN never wins; all
+// -inf gives 0). 1024 threads; 16-byte loads when the vocabulary is a
+// multiple of 4.
+__global__ void __launch_bounds__(1024) k_argmax(const float *logits, int V, int32_t *out) {
+    chain_enter();
     const int m = blockIdx.x;
     const float *l = logits + (size_t)m * V;
     float best = -FLT_MAX;
     int bi = 0;
-    for (int c = threadIdx.x; c < V; c += blockDim.x)
-        if (l[c] > best) { best = l[c]; bi = c; }
+    if ((V & 3) == 0) {
+        const float4 *l4 = reinterpret_cast<const float4 *>(l);
+        for (int c = threadIdx.x; c < V / 4; c += blockDim.x) {
+            const float4 a = l4[c];
+            if (a.x > best) { best = a.x; bi = 4 * c; }
+            if (a.y > best) { best = a.y; bi = 4 * c + 1; }
+            if (a.z > best) { best = a.z; bi = 4 * c + 2; }
+            if (a.w > best) { best = a.w; bi = 4 * c + 3; }
+        }
+    } else {
+        for (int c = threadIdx.x; c < V; c += blockDim.x)
+            if (l[c] > best) { best = l[c]; bi = c; }
+    }
     __shared__ float bv[32];
     __shared__ int bidx[32];
     for (int o = 16; o; o >>= 1) {
@@ -525,8 +622,10 @@ cloak_status serve_step_run(cloak_ctx *ctx, const cloak_serve_desc *d, const clo
                             cudaStream_t s) {
     const bool was = ctx->tune_invariant;
     ctx->tune_invariant = true;
+    ctx->chained = false;
     const cloak_status rc = serve_step_body(ctx, d, b, s);
     ctx->tune_invariant = was;
+    ctx->chained = false;
     return rc;
 }
 
@@ -584,6 +683,14 @@ static cloak_status serve_step_body(cloak_ctx *ctx, const cloak_serve_desc *d,
     float *logits = b->out_logits ? b->out_logits : (float *)take((size_t)std::max(S, 1) * V * 4);
     __nv_bfloat16 *xs = (__nv_bfloat16 *)take((size_t)std::max(S, 1) * D * 2);
     float *apart = (float *)take(part_bytes);
+    const size_t cnt_need = (size_t)std::max(n_single, 1) * HQ;
+    if (cnt_need > ctx->att_cnt_cap) {
+        if (ctx->d_att_cnt) CLOAK_CUDA(ctx, cudaFree(ctx->d_att_cnt));
+        ctx->d_att_cnt = nullptr;
+        CLOAK_CUDA(ctx, cudaMalloc(&ctx->d_att_cnt, cnt_need * 4));
+        CLOAK_CUDA(ctx, cudaMemsetAsync(ctx->d_att_cnt, 0, cnt_need * 4, s));
+        ctx->att_cnt_cap = cnt_need;
+    }
     cloak_status rc;
     if (b->qtiles) {
         static std::atomic<uint64_t> attr_devs{0};  // devices set up
@@ -601,36 +708,56 @@ static cloak_status serve_step_body(cloak_ctx *ctx, const cloak_serve_desc *d,
         k_embed<<<M, 256, 0, s>>>((const __nv_bfloat16 *)d->embedding, b->token_ids, D, V, h);
     }
     CLOAK_LAUNCHED(ctx);
+    // The step's first kernel follows whatever ran before it on the stream (a
+    // table update of a concurrent re-key, the caller's copies); every later
+    // kernel follows one of the step's own, none of which writes the weights or
+    // the tables, so each may start -- a linear fetching its weight tiles --
+    // while its predecessor finishes, and waits for it before reading its output.
+    ctx->chained = true;
+    // h += yy (yy null: no add), then the RMSNorm of n rows (rows null: all)
+    // into xo; one fused kernel where the row fits its registers
+    auto add_norm = [&](const float *yy, const int32_t *rows, int n, __nv_bfloat16 *xo) -> cloak_status {
+        if (D % 4 == 0 && D <= 256 * 4 * NORM_VR) {
+            CLOAK_CUDA(ctx, launch_k(ctx->chained, k_add_rmsnorm<NORM_VR>, dim3(n), dim3(256), 0, s, h, yy, rows,
+                                     D, sd.rms_eps, xo));
+            CLOAK_LAUNCHED(ctx);
+            return CLOAK_OK;
+        }
+        if (yy) {
+            CLOAK_CUDA(ctx, launch_k(ctx->chained, k_add, dim3(nb(Mz * D)), dim3(256), 0, s, h, yy, Mz * D));
+            CLOAK_LAUNCHED(ctx);
+        }
+        CLOAK_CUDA(ctx, launch_k(ctx->chained, k_rmsnorm, dim3(n), dim3(256), 0, s, h, rows, D, sd.rms_eps, xo));
+        CLOAK_LAUNCHED(ctx);
+        return CLOAK_OK;
+    };
+    if (sd.num_layers > 0 && (rc = add_norm(nullptr, nullptr, M, x))) return rc;
     for (int l = 0; l < sd.num_layers; ++l) {
         const int32_t *lt = sd.layer_tensors + 7 * l;
         __nv_bfloat16 *kc = (__nv_bfloat16 *)d->k_cache + (size_t)l * d->num_blocks * 16 * KD;
         __nv_bfloat16 *vc = (__nv_bfloat16 *)d->v_cache + (size_t)l * d->num_blocks * 16 * KD;
-        k_rmsnorm<<<M, 256, 0, s>>>(h, nullptr, D, sd.rms_eps, x);
-        CLOAK_LAUNCHED(ctx);
         {
             const int32_t ts[3] = {lt[0], lt[1], lt[2]};
             const void *xs3[3] = {x, x, x};
             void *ys3[3] = {q, k, v};
             if ((rc = step_linears(ctx, 3, ts, xs3, ys3, M, m_dec, CLOAK_OUT_BF16, flags, s))) return rc;
         }
-        k_rope_cache<<<dim3(M, HQ + HKV), 64, 0, s>>>(q, k, v, b->positions, b->req_slots, b->block_tables,
-                                                      d->max_blocks, HQ, HKV, d->rope_theta, kc, vc);
+        CLOAK_CUDA(ctx, launch_k(ctx->chained, k_rope_cache, dim3(M, HQ + HKV), dim3(64), 0, s, q, k, v,
+                                 b->positions, b->req_slots, b->block_tables, d->max_blocks, HQ, HKV,
+                                 d->rope_theta, kc, vc));
         CLOAK_LAUNCHED(ctx);
         if (b->qtiles && b->num_qtiles > 0) {
             // prefill runs: query tiles sharing staged K/V tiles
-            k_attention_tiled<<<dim3(b->num_qtiles, HQ), 128, 4 * ATT_TILE_BYTES, s>>>(
-                q, kc, vc, b->positions, b->req_slots, b->block_tables, b->qtiles, d->max_blocks, HQ,
-                HKV, attn);
+            CLOAK_CUDA(ctx, launch_k(ctx->chained, k_attention_tiled, dim3(b->num_qtiles, HQ), dim3(128),
+                                     4 * ATT_TILE_BYTES, s, q, kc, vc, b->positions, b->req_slots,
+                                     b->block_tables, b->qtiles, d->max_blocks, HQ, HKV, attn));
             CLOAK_LAUNCHED(ctx);
         }
         if (n_single > 0) {
             // single queries (all tokens without a work split): split over the keys
-            k_attn_decode<<<dim3(max_splits, n_single, HQ), 128, 0, s>>>(
-                q, kc, vc, b->positions, b->req_slots, b->block_tables, single, d->max_blocks, HQ, HKV,
-                max_splits, apart, attn);
-            CLOAK_LAUNCHED(ctx);
-            k_attn_combine<<<dim3(n_single, HQ), 128, 0, s>>>(b->positions, single, HQ, max_splits, apart,
-                                                              attn);
+            CLOAK_CUDA(ctx, launch_k(ctx->chained, k_attn_decode, dim3(std::min(max_splits, ATT_GRID_X), n_single, HQ),
+                                     dim3(128), 0, s, q, kc, vc, b->positions, b->req_slots, b->block_tables,
+                                     single, d->max_blocks, HQ, HKV, max_splits, apart, ctx->d_att_cnt, attn));
             CLOAK_LAUNCHED(ctx);
         }
         {
@@ -639,17 +766,15 @@ static cloak_status serve_step_body(cloak_ctx *ctx, const cloak_serve_desc *d,
             void *y1[1] = {y};
             if ((rc = step_linears(ctx, 1, t1, x1, y1, M, m_dec, CLOAK_OUT_F32, flags, s))) return rc;
         }
-        k_add<<<nb(Mz * D), 256, 0, s>>>(h, y, Mz * D);
-        CLOAK_LAUNCHED(ctx);
-        k_rmsnorm<<<M, 256, 0, s>>>(h, nullptr, D, sd.rms_eps, x);
-        CLOAK_LAUNCHED(ctx);
+        if ((rc = add_norm(y, nullptr, M, x))) return rc;
         {
             const int32_t ts[2] = {lt[4], lt[5]};
             const void *xs2[2] = {x, x};
             void *ys2[2] = {g, u};
             if ((rc = step_linears(ctx, 2, ts, xs2, ys2, M, m_dec, CLOAK_OUT_F32, flags, s))) return rc;
         }
-        k_silu_mul<<<nb(Mz * F), 256, 0, s>>>(g, u, act, Mz * F);
+        CLOAK_CUDA(ctx, launch_k(ctx->chained, k_silu_mul, dim3(nb(Mz * F)), dim3(256), 0, s, g, u, act,
+                                 Mz * F));
         CLOAK_LAUNCHED(ctx);
         {
             const int32_t t1[1] = {lt[6]};
@@ -657,14 +782,18 @@ static cloak_status serve_step_body(cloak_ctx *ctx, const cloak_serve_desc *d,
             void *y1[1] = {y};
             if ((rc = step_linears(ctx, 1, t1, x1, y1, M, m_dec, CLOAK_OUT_F32, flags, s))) return rc;
         }
-        k_add<<<nb(Mz * D), 256, 0, s>>>(h, y, Mz * D);
-        CLOAK_LAUNCHED(ctx);
+        // the next layer's input norm, or after the last layer the final norm
+        // of the sampled rows (nothing reads the other rows of h after it)
+        if (l + 1 < sd.num_layers) {
+            if ((rc = add_norm(y, nullptr, M, x))) return rc;
+        } else if (S > 0) {
+            if ((rc = add_norm(y, b->sample_rows, S, xs))) return rc;
+        }
     }
     if (S > 0) {
-        k_rmsnorm<<<S, 256, 0, s>>>(h, b->sample_rows, D, sd.rms_eps, xs);
-        CLOAK_LAUNCHED(ctx);
+        if (sd.num_layers == 0 && (rc = add_norm(nullptr, b->sample_rows, S, xs))) return rc;
         if ((rc = linear_run(ctx, d->lm_head, xs, logits, S, CLOAK_OUT_F32, flags, s))) return rc;
-        k_argmax<<<S, 256, 0, s>>>(logits, V, b->out_tokens);
+        CLOAK_CUDA(ctx, launch_k(ctx->chained, k_argmax, dim3(S), dim3(1024), 0, s, logits, V, b->out_tokens));
         CLOAK_LAUNCHED(ctx);
     }
     return CLOAK_OK;

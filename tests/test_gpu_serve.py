@@ -87,6 +87,30 @@ def test_serve_step_matches_full_model_oracle(served, tiled, decode_first):
             assert seq[23 + step] == int(np.argmax(ref[p]))
 
 
+def test_decode_attention_over_a_long_context(cloak_lib):
+    """A prompt of 1,100 tokens: each decode token attends over 18 key
+    splits, more than the blocks of one (token, head), so blocks take several
+    splits and the last to finish merges them. Logits against the FP64 model;
+    the request alone equals the request next to a short one."""
+    m = small_served()
+    Ws = synth.weights_host(m, seed=0, std=0.05)
+    sm = serve.ServedModel(m, kv_blocks=256, max_blocks=80, twin=True, weights=Ws)
+    long = list(np.random.default_rng(11).integers(0, 1000, 1100))
+    short = list(np.random.default_rng(12).integers(0, 1000, 40))
+    la, sa = run_steps(sm, [(0, long)], tiled=True)
+    lm, _ = run_steps(sm, [(1, short), (0, long)], tiled=True)
+    for x, y in zip(la[0], lm[0]):
+        assert np.array_equal(x, y)
+    W64 = [O.bf16_value(O.bf16_bits(w)) for w in Ws]
+    emb64 = O.bf16_value(O.bf16_bits(synth.embedding_host(1000, 512)))
+    seq = sa[0]
+    ref = O.transformer_logits_f64(m, W64, emb64, seq[:-1])
+    for step, lg in enumerate(la[0]):
+        p = 1099 + step
+        assert O.relative_error(lg, ref[p]) <= 1e-2, (step, O.relative_error(lg, ref[p]))
+    sm.close()
+
+
 @pytest.mark.parametrize("tiled", [False, True])
 def test_request_alone_equals_request_in_a_mix(served, tiled):
     m, Ws, sm = served
