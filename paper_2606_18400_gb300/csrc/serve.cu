@@ -331,14 +331,18 @@ __global__ void __launch_bounds__(128) k_attn_decode(const __nv_bfloat16 *q, con
         // the last split of (token, head) to finish merges all of them, in
         // split order (the same arithmetic whichever block it is), and resets
         // the count; its arrival is the block's last (every split has arrived)
-        __threadfence();
+        // (the block's stores are ordered before thread 0's fence by the
+        // barrier; the fence makes them visible before the arrival)
         __syncthreads();  // also: wm, wl, wa are free for the next split
-        if (t == 0) last = atomicAdd(cnt + (size_t)r * HQ + j, 1u) == (uint32_t)nsplit - 1;
+        if (t == 0) {
+            __threadfence();
+            last = atomicAdd(cnt + (size_t)r * HQ + j, 1u) == (uint32_t)nsplit - 1;
+            if (last) __threadfence();
+        }
         __syncthreads();
         if (last) break;
     }
     if (nsplit == 1 || !last) return;
-    __threadfence();
     float Mx = -FLT_MAX;
     for (int q = 0; q < nsplit; ++q) Mx = fmaxf(Mx, __ldcg(pb + q * ATT_PART));
     float Ls = 0.0f, As = 0.0f;
