@@ -285,13 +285,14 @@ def bench_extras(cloak, synth, torch, dev, stream, key, steps, tune=True, serve_
         torch.cuda.synchronize()
         return a.elapsed_time(b) / K
 
-    def graph(fn):
+    def graph(fn, n=1):
         fn()
         fn()
         torch.cuda.synchronize()
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g, stream=stream):
-            fn()
+            for _ in range(n):
+                fn()
         return g
 
     def layer_run(cm, model, M, seed0):
@@ -303,13 +304,15 @@ def bench_extras(cloak, synth, torch, dev, stream, key, steps, tune=True, serve_
         if tune:
             res["launch_shape"] = tuned_shape(cm.autotune(list(range(T)), xs, ys, out_dtype=cloak.OUT_BF16,
                                                           stream=stream.cuda_stream))
+        # 10 consecutive chained steps per graph replay (the prefill GEMM
+        # ignores the flag: its launches follow one another)
         for name, flags in (("cloaked", 0), ("uncloaked", cloak.LINEAR_UNCLOAKED)):
             def fn(flags=flags):
                 cloak.cloak_linear_batch(cm.ctx, list(range(T)), [x.data_ptr() for x in xs],
-                                         [y.data_ptr() for y in ys], M, cloak.OUT_BF16, flags,
-                                         stream.cuda_stream)
-            g = graph(fn)
-            res[name] = timed(g.replay, max(10, steps // 4))
+                                         [y.data_ptr() for y in ys], M, cloak.OUT_BF16,
+                                         flags | cloak.LINEAR_CHAINED, stream.cuda_stream)
+            g = graph(fn, 10)
+            res[name] = timed(g.replay, max(2, steps // 40)) / 10
             del g
         return res
 
@@ -725,22 +728,43 @@ def run_cloak(args):
 
     tensors = list(range(T))
 
-    def step_fn(xs, ys, M, unc):
+    def step_fn(xs, ys, M, unc, chained=False):
         # one launch: the seven linears' tiles split evenly over the SMs
-        flags = cloak.LINEAR_UNCLOAKED if unc else 0
+        flags = (cloak.LINEAR_UNCLOAKED if unc else 0) | (cloak.LINEAR_CHAINED if chained else 0)
         cloak.cloak_linear_batch(cm.ctx, tensors, [x.data_ptr() for x in xs],
                                  [y.data_ptr() for y in ys], M, cloak.OUT_BF16, flags,
                                  stream.cuda_stream)
 
-    def graph_of(xs, ys, M, unc):
+    def graph_of(xs, ys, M, unc, n=1, chained=False):
         for _ in range(2):
-            step_fn(xs, ys, M, unc)  # allocate workspaces outside the capture
+            step_fn(xs, ys, M, unc, chained)  # allocate workspaces outside the capture
         torch.cuda.synchronize()
         g = torch.cuda.CUDAGraph()
         n0 = cm.launches()
         with torch.cuda.graph(g, stream=stream):
-            step_fn(xs, ys, M, unc)
-        return g, cm.launches() - n0
+            for _ in range(n):
+                step_fn(xs, ys, M, unc, chained)
+        return g, (cm.launches() - n0) // n
+
+    def time_chain(xs, ys, M, unc, K, W):
+        """K consecutive steps as chained launches (each launch streams its
+        weights while the previous one finishes and reads x after it has
+        completed), captured in one graph and replayed once after a W-step
+        warm-up graph: the timed region is exactly K steps."""
+        gw, _ = graph_of(xs, ys, M, unc, W, True)
+        gk, lps = graph_of(xs, ys, M, unc, K, True)
+        gw.replay()
+        torch.cuda.synchronize()
+        barrier(ws)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        gk.replay()
+        b.record()
+        torch.cuda.synchronize()
+        barrier(ws)
+        del gw, gk
+        return max_over_ranks(a.elapsed_time(b) / K, ws), lps
 
     def time_graph(g, K, W):
         for _ in range(W):
@@ -764,10 +788,13 @@ def run_cloak(args):
     if not args.no_tune:  # launch shape from the autotuner (measured here, on this GPU)
         shape = tuned_shape(cm.autotune(list(range(T)), xs, ys, out_dtype=cloak.OUT_BF16,
                                         stream=stream.cuda_stream))
-    g_cl, launches_per_step = graph_of(xs, ys, M, False)
-    g_un, _ = graph_of(xs, ys, M, True)
-    ms = time_graph(g_cl, args.steps, args.warmup)
-    ms_un = time_graph(g_un, args.steps, args.warmup)
+    ms, launches_per_step = time_chain(xs, ys, M, False, args.steps, args.warmup)
+    ms_un, _ = time_chain(xs, ys, M, True, args.steps, args.warmup)
+    # the same steps unchained: one graph replay per step, each launch
+    # starting after the previous one has completed
+    g_cl, _ = graph_of(xs, ys, M, False)
+    ms_plain = time_graph(g_cl, args.steps, args.warmup)
+    del g_cl
     B = step_bytes(model, M)
     value = job_rate(B, ms, ws) / 1e9
 
@@ -817,16 +844,14 @@ def run_cloak(args):
         if not args.no_tune:
             sh = tuned_shape(cm.autotune(list(range(T)), xs2, ys2, out_dtype=cloak.OUT_BF16,
                                          stream=stream.cuda_stream))
-        gc, _ = graph_of(xs2, ys2, Ms, False)
-        gu, _ = graph_of(xs2, ys2, Ms, True)
-        mc = time_graph(gc, max(20, args.steps), 3)
-        mu = time_graph(gu, max(20, args.steps), 3)
+        mc, _ = time_chain(xs2, ys2, Ms, False, max(20, args.steps), 3)
+        mu, _ = time_chain(xs2, ys2, Ms, True, max(20, args.steps), 3)
         Bs = step_bytes(model, Ms)
         sweep[str(Ms)] = {"cloaked_gbs": round(Bs / (mc / 1e3) / 1e9, 1),
                           "uncloaked_gbs": round(Bs / (mu / 1e3) / 1e9, 1),
                           "cloaked_us": round(mc * 1e3, 2), "uncloaked_us": round(mu * 1e3, 2),
                           "launch_shape": sh}
-        del gc, gu, xs2, ys2
+        del xs2, ys2
 
     # end to end through the C ABI with host buffers (copies inside the timing):
     # the step's seven input vectors packed in one pinned buffer, its seven
@@ -896,7 +921,10 @@ def run_cloak(args):
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "batch": M, "weight_bytes": sum(t.n * t.k * 2 for t in model.tensors),
                        "bytes_per_step": B, "tiles": cm.G, "pages": cm.NP, "spare_pages": model.spare_pages,
-                       "launch": "CUDA graph of one grouped launch (7 linears) per step",
+                       "launch": "one grouped launch (7 linears) per step; the K timed steps are K "
+                                 "consecutive chained launches (CLOAK_LINEAR_CHAINED) in one CUDA graph: "
+                                 "each launch streams its weight tiles while the previous one finishes "
+                                 "and reads x after it has completed",
                        "launch_shape": shape,
                        "l2": "inputs larger than L2: 404.75 MB of weights per step vs 129 MB L2"},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
@@ -904,8 +932,11 @@ def run_cloak(args):
                          "traffic": traffic, "peak_source": peak_note,
                          "kernel": "k_linear_tc<bf16, N=16>: one launch, 7 linears, swap-AB tcgen05, stream-K",
                          "kernel_us": round(ms * 1e3, 2),
-                         "kernel_us_source": "CUDA events around the timed region's graph replays "
-                                             "(one launch of the kernel per step), divided by the steps",
+                         "kernel_us_source": "CUDA events around the timed region (one replay of a graph "
+                                             "of K chained launches, one per step), divided by the steps",
+                         "kernel_us_unchained": round(ms_plain * 1e3, 2),
+                         "kernel_us_unchained_source": "one graph replay per step (each launch starts "
+                                                       "after the previous one completed)",
                          "kernel_us_bracketed": round(kern_ms * 1e3, 2)},
             "cpu_baseline": cpu,
             "e2e": {"value": round(job_rate(B, e2e_ms, ws) / 1e9, 2), "unit": "GB/s",
@@ -1054,7 +1085,7 @@ def run_profile(args):
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_push("profiled")
         for _ in range(3):
-            cm.linear_batch(group, xs)
+            cm.linear_batch(group, xs, chained=True)  # as the timed steps launch it
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
         print(json.dumps({"launch_shape": shape}))

@@ -231,7 +231,7 @@ enum {
     CLOAK_LINEAR_UNCLOAKED = 1,  /* run the same kernel on the twin, tiles
                                     addressed arithmetically (tile-major)    */
     CLOAK_LINEAR_RELU = 2,       /* y = max(y, 0)                             */
-    CLOAK_LINEAR_VMM = 8         /* CLOAK_MODEL_VMM contexts: run the same
+    CLOAK_LINEAR_VMM = 8,        /* CLOAK_MODEL_VMM contexts: run the same
                                     kernel on the virtual view, each tile
                                     found at its virtual position (the tile
                                     permutation); the MMU supplies the page
@@ -240,6 +240,24 @@ enum {
                                     read. Not with CLOAK_LINEAR_UNCLOAKED, and
                                     CLOAK_E_STATE while a concurrent re-key
                                     is in progress.                          */
+    CLOAK_LINEAR_CHAINED = 16    /* cloak_linear / cloak_linear_batch on a
+                                    BF16 or E4M3 model: a programmatic
+                                    dependent launch. Its CTAs may start
+                                    while the kernel enqueued before it on
+                                    the stream is still running and fetch
+                                    weight tiles at once; they read x, the
+                                    scratch and y only after that kernel has
+                                    completed (griddepcontrol.wait). The
+                                    caller asserts that the kernel before it
+                                    on the stream writes none of this
+                                    context's weights, tables or scales
+                                    (another linear call, or the caller's
+                                    own kernels producing x, qualify;
+                                    shuffle, upload, re-key and a concurrent
+                                    re-key's table update do not). Results
+                                    are bit for bit those without the flag.
+                                    Prefill-shaped batches (whole-tile GEMM)
+                                    and FP32 models ignore it.               */
 };
 enum { CLOAK_OUT_F32 = 0, CLOAK_OUT_BF16 = 1 };
 

@@ -20,7 +20,7 @@ OK, E_INVAL, E_NOMEM, E_CUDA, E_TIMEOUT, E_STATE, E_UNSUPPORTED, E_DRAWS = 0, -1
 F32, BF16, E4M3 = 0, 1, 2
 MODEL_TWIN, MODEL_VMM, MODEL_TILE_REKEY = 1, 2, 4
 TAB_LAYER_PERM, TAB_GROUP_PERM, TAB_TENSOR_BASE, TAB_TILE_PERM, TAB_PAGE_ALLOC, TAB_TILE_SLOT = range(6)
-LINEAR_UNCLOAKED, LINEAR_RELU, LINEAR_VMM = 1, 2, 8
+LINEAR_UNCLOAKED, LINEAR_RELU, LINEAR_VMM, LINEAR_CHAINED = 1, 2, 8, 16
 SERVE_DECODE_FIRST = 4
 OUT_F32, OUT_BF16 = 0, 1
 
@@ -438,26 +438,26 @@ class CloakModel:
                             self.device).clone()
 
     def linear(self, t, x, y=None, out_dtype=OUT_BF16, uncloaked=False, relu=False, stream=None,
-               vmm=False):
+               vmm=False, chained=False):
         import torch
         tt = self.model.tensors[t]
         M = x.shape[0]
         if y is None:
             y = torch.empty((M, tt.n), device=x.device,
                             dtype=torch.float32 if out_dtype == OUT_F32 else torch.bfloat16)
-        flags = _storage(uncloaked, vmm) | (LINEAR_RELU if relu else 0)
+        flags = _storage(uncloaked, vmm) | (LINEAR_RELU if relu else 0) | (LINEAR_CHAINED if chained else 0)
         cloak_linear(self.ctx, t, x.data_ptr(), y.data_ptr(), M, out_dtype, flags, stream)
         return y
 
     def linear_batch(self, tensors, xs, ys=None, out_dtype=OUT_BF16, uncloaked=False, relu=False,
-                     stream=None, vmm=False):
+                     stream=None, vmm=False, chained=False):
         import torch
         M = xs[0].shape[0]
         if ys is None:
             ys = [torch.empty((M, self.model.tensors[t].n), device=xs[0].device,
                               dtype=torch.float32 if out_dtype == OUT_F32 else torch.bfloat16)
                   for t in tensors]
-        flags = _storage(uncloaked, vmm) | (LINEAR_RELU if relu else 0)
+        flags = _storage(uncloaked, vmm) | (LINEAR_RELU if relu else 0) | (LINEAR_CHAINED if chained else 0)
         cloak_linear_batch(self.ctx, list(tensors), [x.data_ptr() for x in xs],
                            [y.data_ptr() for y in ys], M, out_dtype, flags, stream)
         return ys

@@ -412,7 +412,7 @@ extern "C" cloak_status cloak_linear(cloak_ctx *ctx, int32_t tensor, const void 
                                      void *stream) {
     if (!ctx || !x_dev || !y_dev || tensor < 0 || tensor >= (int32_t)ctx->tensors.size() ||
         M < 1 || M > 65536 || (out_dtype != CLOAK_OUT_F32 && out_dtype != CLOAK_OUT_BF16) ||
-        (flags & ~(3 | CLOAK_LINEAR_VMM)) || ((uintptr_t)x_dev & 15))
+        (flags & ~(3 | CLOAK_LINEAR_VMM | CLOAK_LINEAR_CHAINED)) || ((uintptr_t)x_dev & 15))
         return CLOAK_E_INVAL;
     if (!ctx->keyed) return CLOAK_E_STATE;
     if (cloak_status rc = storage_ok(ctx, flags)) return rc;
@@ -423,7 +423,8 @@ extern "C" cloak_status cloak_linear_batch(cloak_ctx *ctx, int32_t n, const int3
                                            const void *const *x_dev, void *const *y_dev, int32_t M,
                                            int32_t out_dtype, int32_t flags, void *stream) {
     if (!ctx || n < 1 || n > 8 || !tensors || !x_dev || !y_dev || M < 1 || M > 65536 ||
-        (out_dtype != CLOAK_OUT_F32 && out_dtype != CLOAK_OUT_BF16) || (flags & ~(3 | CLOAK_LINEAR_VMM)))
+        (out_dtype != CLOAK_OUT_F32 && out_dtype != CLOAK_OUT_BF16) ||
+        (flags & ~(3 | CLOAK_LINEAR_VMM | CLOAK_LINEAR_CHAINED)))
         return CLOAK_E_INVAL;
     for (int i = 0; i < n; ++i) {
         if (tensors[i] < 0 || tensors[i] >= (int32_t)ctx->tensors.size() || !x_dev[i] || !y_dev[i] ||

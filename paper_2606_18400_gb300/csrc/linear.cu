@@ -108,6 +108,7 @@ struct QuantJobs {
 // one launch for every problem of a batch: block (r, p) quantises row r of x_p
 __global__ void __launch_bounds__(256) k_quant_rows_multi(QuantJobs j) {
     griddep_launch_dependents();  // the linear may start (and fetch weights) now
+    griddep_wait();               // as a chained launch: x and the scratch after the previous kernel
     const int p = blockIdx.y;
     const int64_t r = blockIdx.x;
     const int K = j.K[p];
@@ -452,7 +453,7 @@ __global__ void __launch_bounds__(192, 1)
         const int qd = warp & 3;
         const int r_in = qd * 32 + lane;
         const int et = threadIdx.x - 64;  // 0..127
-        if (b.dep_wait) griddep_wait();  // the activation scales come from the quantiser
+        if (b.dep_wait) griddep_wait();  // x, its scales, the scratch: after the previous kernel
         if (FP8 && b.fuse_quant) {
             // Decode batches (M <= 4): quantise the activations of the problems
             // this CTA's range touches into its own slice of the scratch, per
@@ -798,6 +799,8 @@ cloak_status linear_batch_run(cloak_ctx *ctx, int n, const int32_t *tensors, con
         const int mb = std::min(chunk, M - m0);
         TcBatch b{};
         b.slot_of = slot_of;
+        // the weight ring fills while the stream's previous kernel finishes
+        b.dep_wait = (flags & CLOAK_LINEAR_CHAINED) ? 1 : 0;
         b.np = n;
         b.M = mb;
         b.out_f32 = out_dtype == CLOAK_OUT_F32;
@@ -845,7 +848,8 @@ cloak_status linear_batch_run(cloak_ctx *ctx, int n, const int32_t *tensors, con
         b.total = u;
         b.fuse_quant = fuse ? 1 : 0;
         if (fp8 && !fuse) {
-            k_quant_rows_multi<<<dim3(mb, n), 256, 0, s>>>(qj);
+            CLOAK_CUDA(ctx, launch_k(b.dep_wait || ctx->chained, k_quant_rows_multi, dim3(mb, n), dim3(256), 0, s,
+                                     qj));
             CLOAK_LAUNCHED(ctx);
             b.dep_wait = 1;
         }

@@ -340,3 +340,59 @@ def test_full_fp8_gqa_layer_sampled(cloak_lib, M):
         assert np.array_equal(sc.view(np.uint32), s.view(np.uint32)), t  # the same row scales
     assert cm.device_status() == 0
     cm.close()
+
+
+@pytest.mark.parametrize("fp8,M", [(False, 1), (False, 16), (True, 1), (True, 16)])
+def test_chained_launches_equal_plain_ones(cloak_lib, fp8, M):
+    """A chain of 24 dependent linears (Wq, then Wo on its output, then Wq
+    on that, ...; BF16 outputs feeding the next call) launched as chained
+    launches -- each one's CTAs stream weights while the previous one runs and
+    read x after it completes -- gives the plain chain's result bit for bit,
+    eagerly and replayed from a CUDA graph. E4M3 at M = 1 quantises inside the
+    launch, at M = 16 in a separate kernel before it."""
+    m = synth.gqa28_fp8(1) if fp8 else synth.llama7b_layer(1)
+    cm = cloak_lib.CloakModel(m)
+    cm.keygen(0x77, 0)
+    for t in range(len(m.tensors)):
+        cm.shuffle(t, synth.weights_device(m, t, seed=4))
+    kinds = {tt.kind: i for i, tt in enumerate(m.tensors)}
+    tq, to = kinds[synth.K_Q], kinds[synth.K_O]
+    assert m.tensors[tq].n == m.tensors[to].k and m.tensors[to].n == m.tensors[tq].k
+    x0 = x_device(m, synth.activations_host(M, m.tensors[tq].k, seed=3))
+    s = torch.cuda.Stream()
+    bufs = [torch.empty((M, m.tensors[tq if i % 2 == 0 else to].n), dtype=torch.bfloat16, device="cuda")
+            for i in range(24)]
+
+    def chain(chained):
+        x = x0
+        for i in range(24):
+            t = tq if i % 2 == 0 else to
+            y = bufs[i]
+            cm.linear(t, x, y, out_dtype=cloak_lib.OUT_BF16, stream=s.cuda_stream, chained=chained)
+            x = y
+        return x
+
+    with torch.cuda.stream(s):
+        ref = torch_bf16_bits(chain(False))
+        torch.cuda.synchronize()
+        for b in bufs:
+            b.zero_()
+        got = torch_bf16_bits(chain(True))
+        torch.cuda.synchronize()
+    assert np.array_equal(ref, got)
+    for b in bufs:
+        b.zero_()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        out = chain(True)
+    for _ in range(3):
+        for b in bufs:
+            b.zero_()
+        torch.cuda.synchronize()
+        g.replay()
+        torch.cuda.synchronize()
+        assert np.array_equal(ref, torch_bf16_bits(out))
+    assert torch.isfinite(out.float()).all()
+    assert cm.device_status() == 0
+    cm.close()
