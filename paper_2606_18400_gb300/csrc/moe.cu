@@ -26,6 +26,7 @@
 #include <vector>
 
 #include "internal.cuh"
+#include "ptx.cuh"
 
 namespace cloak {
 
@@ -61,6 +62,8 @@ __global__ void __launch_bounds__(256) k_moe_route(const float *rpart, int rkc, 
     __shared__ int ls[MOE_MAX_E];
     __shared__ float pz[MOE_MAX_K];
     __shared__ int pick[MOE_MAX_K];
+    griddep_launch_dependents();  // the gate/up launch may be scheduled now
+    griddep_wait();               // the router partials are the previous kernel's
     const int m = blockIdx.x;
     const size_t R = (size_t)((E + 127) / 128) * 128;
     for (int e = threadIdx.x; e < E; e += blockDim.x) {
@@ -127,6 +130,12 @@ __global__ void __launch_bounds__(256) k_moe_route(const float *rpart, int rkc, 
 // found with a self-resetting counter, sums the group's partials in a fixed
 // order): ROUTER none; GATE_UP act = bf16(silu(g) * u) for the tile row;
 // DOWN y = sum_j w_j down_j for the tile row.
+// The step's launches after the router are chained (programmatic dependent
+// launches): ROUTER and DOWN trigger their dependents at entry; the routing
+// kernel too; GATE_UP waits for the routing first and triggers only then, so
+// the routing is final before any DOWN block starts. DOWN looks up its tiles
+// and loads the first one (the rest of its chunk pulled into L2) before it
+// waits for GATE_UP's activations.
 enum { EP_ROUTER = 0, EP_GATE_UP = 1, EP_DOWN = 2 };
 
 struct GemvArgs {
@@ -154,7 +163,13 @@ __global__ void __launch_bounds__(256) k_moe_gemv(GemvArgs a) {
     const int nt = b % a.nt_n; b /= a.nt_n;
     const int mi = b % a.nmat;
     const int p = b / a.nmat;
-    const uint32_t base = EP == EP_ROUTER ? a.base0 : a.tab[a.sel[p] * 3 + a.mat0 + mi];
+    if constexpr (EP == EP_GATE_UP) {
+        griddep_wait();               // the routing
+        griddep_launch_dependents();  // DOWN may start: the routing is final
+    } else {
+        griddep_launch_dependents();
+    }
+    const uint32_t base = EP == EP_ROUTER ? a.base0 : a.tab[__ldcg(a.sel + p) * 3 + a.mat0 + mi];
     const __nv_bfloat16 *x = a.x + (size_t)(a.x_per_token ? p / a.K : p) * a.xs;
     const int t = threadIdx.x, c = (t & 15) * 8;
     float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -176,6 +191,12 @@ __global__ void __launch_bounds__(256) k_moe_gemv(GemvArgs a) {
 #pragma unroll
         for (int it = 0; it < 8; ++it) wv[it] = __ldcs(tile + it * 256 + t);
     }
+    if constexpr (EP == EP_DOWN) {
+        // the chunk's other tiles into L2 (one 128-byte line per thread per tile)
+        for (int kt = k0 + 1; kt < k1; ++kt)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<const uint8_t *>(tile_of(kt)) + t * 128));
+    }
+    if constexpr (EP != EP_GATE_UP) griddep_wait();  // x / act: the previous kernel's
     for (int kt = k0; kt < k1; ++kt) {
         uint4 nv[8];
         if (kt + 1 < k1) {
@@ -344,15 +365,13 @@ cloak_status moe_run(cloak_ctx *ctx, const cloak_moe_desc *d, const void *x, flo
     g.kc_n = rkc;
     g.ks = (DT + rkc - 1) / rkc;
     g.part = rp;
+    // (an ordinary launch: the kernel before it may have written the weights)
     k_moe_gemv<EP_ROUTER><<<M * ET * rkc, 256, 0, s>>>(g);
     CLOAK_LAUNCHED(ctx);
-    // 2. routing
-    if (E <= 128)
-        k_moe_route<4><<<M, 256, 0, s>>>(rp, rkc, gp, E, K, sel, w, logits_out, experts_out);
-    else if (E <= 256)
-        k_moe_route<8><<<M, 256, 0, s>>>(rp, rkc, gp, E, K, sel, w, logits_out, experts_out);
-    else
-        k_moe_route<32><<<M, 256, 0, s>>>(rp, rkc, gp, E, K, sel, w, logits_out, experts_out);
+    // 2. routing (this and the later launches are chained)
+    auto route = E <= 128 ? k_moe_route<4> : E <= 256 ? k_moe_route<8> : k_moe_route<32>;
+    CLOAK_CUDA(ctx, launch_k(true, route, dim3(M), dim3(256), 0, s, (const float *)rp, rkc, gp, E, K, sel, w,
+                             logits_out, experts_out));
     CLOAK_LAUNCHED(ctx);
     // 3-4. gate and up of the selected experts; the last block of a tile row writes act
     g.x_per_token = 1;
@@ -366,7 +385,7 @@ cloak_status moe_run(cloak_ctx *ctx, const cloak_moe_desc *d, const void *x, flo
     g.cnt = cnt;
     g.act = act;
     g.rows = F;
-    k_moe_gemv<EP_GATE_UP><<<pairs * 2 * FT * kc1, 256, 0, s>>>(g);
+    CLOAK_CUDA(ctx, launch_k(true, k_moe_gemv<EP_GATE_UP>, dim3(pairs * 2 * FT * kc1), dim3(256), 0, s, g));
     CLOAK_LAUNCHED(ctx);
     // 5-6. down; the last block of a token's tile row writes y
     g.x = act;
@@ -383,7 +402,7 @@ cloak_status moe_run(cloak_ctx *ctx, const cloak_moe_desc *d, const void *x, flo
     g.w = w;
     g.y = y;
     g.rows = D;
-    k_moe_gemv<EP_DOWN><<<pairs * DT * kc2, 256, 0, s>>>(g);
+    CLOAK_CUDA(ctx, launch_k(true, k_moe_gemv<EP_DOWN>, dim3(pairs * DT * kc2), dim3(256), 0, s, g));
     CLOAK_LAUNCHED(ctx);
     return CLOAK_OK;
 }
