@@ -256,6 +256,8 @@ enum {
                                     shuffle, upload, re-key and a concurrent
                                     re-key's table update do not). Results
                                     are bit for bit those without the flag.
+                                    E4M3 decode batches then quantise x in a
+                                    separate kernel, chained the same way.
                                     Prefill-shaped batches (whole-tile GEMM)
                                     and FP32 models ignore it.               */
 };

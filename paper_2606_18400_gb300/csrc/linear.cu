@@ -781,8 +781,10 @@ cloak_status linear_batch_run(cloak_ctx *ctx, int n, const int32_t *tensors, con
         return gemm_run(ctx, n, tensors, xg, sg, ys, M, out_dtype == CLOAK_OUT_F32, relu, slot_of, tw, s);
     }
     // E4M3 decode batches quantise their activations inside the linear (each
-    // CTA for the problems it touches); this needs K a multiple of 16
-    bool fuse = fp8 && M <= 4;
+    // CTA for the problems it touches); this needs K a multiple of 16. A
+    // chained launch takes the separate quantiser instead, itself chained: the
+    // linear's weight ring fills while it runs (measured faster at M = 1..4)
+    bool fuse = fp8 && M <= 4 && !(flags & CLOAK_LINEAR_CHAINED);
     for (int p = 0; p < n && fuse; ++p) fuse = ctx->info[tensors[p]].k % 16 == 0;
     if (fp8 && !fuse) {
         size_t qb = 0;
