@@ -269,10 +269,24 @@ __global__ void __launch_bounds__(256) k_moe_gemv(GemvArgs a) {
     }
 }
 
-// K chunks: as many as keep the launch within one wave of two CTAs per SM
-// (the GEMV's register use), at most `cap` (the epilogues' unrolled sums)
+// K chunks (at most `cap`: the epilogues' unrolled sums): the count whose
+// waves of two CTAs per SM (the GEMV's register use) take the least time,
+// a block costing its tiles plus about three tiles' worth of fixed latency
+// (table lookup, first load, arrival); fewer chunks on a tie
 int chunks_for(int blocks_per_chunk, int kt_n, int sms, int cap) {
-    return std::max(1, std::min(std::min(kt_n, cap), 2 * sms / blocks_per_chunk));
+    int best = 1;
+    long best_t = -1;
+    for (int kc = 1; kc <= std::min(kt_n, cap); ++kc) {
+        const int ks = (kt_n + kc - 1) / kc;
+        if ((kt_n + ks - 1) / ks != kc) continue;  // the same split as a smaller count
+        const long waves = ((long)blocks_per_chunk * kc + 2 * sms - 1) / (2 * sms);
+        const long t = waves * (ks + 3);
+        if (best_t < 0 || t < best_t) {
+            best_t = t;
+            best = kc;
+        }
+    }
+    return best;
 }
 
 }  // namespace
