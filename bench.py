@@ -1037,7 +1037,10 @@ def run_profile(args):
     prefill-- one 7B-class layer, grouped M=2048 (the prefill GEMM), 3 launches;
     decode -- one 7B-class layer, grouped M=1 (the headline step), 3 launches;
     moe    -- one MoE block of the Qwen3-30B-A3B shape (1.2 GB), decode M=1,
-              3 steps (4 kernels each), a different token per step.
+              3 steps (4 kernels each), a different token per step;
+    serve  -- the 32-layer served model (13.4 GB) with --M requests of 1,000-token
+              prompts prefilled, then one decode-only step (all kernels of the step;
+              for launch lists: the KV cache makes it up to 35 GB at --M 64).
     The linears' launch shape is tuned first (unless --no-tune); the profiled
     launches sit inside the NVTX range "profiled" (ncu --nvtx
     --nvtx-include "profiled/")."""
@@ -1045,6 +1048,33 @@ def run_profile(args):
     from paper_2606_18400_gb300 import cloak, synth
     cloak.load()
     torch.cuda.set_device(0)
+    if args.profile == "serve":
+        from paper_2606_18400_gb300 import serve
+        B = args.M
+        sm = serve.ServedModel(synth.serving_model(32, 32000), kv_blocks=B * 66 + 8, max_blocks=66,
+                               twin=False)
+        srv = serve.Server(sm, max_running=64, token_budget=2048, rekey_period=None)
+        rng = np.random.default_rng(B)
+        reqs = [serve.Request(i, 0.0, rng.integers(0, 32000, 1000).astype(np.int32), 40) for i in range(B)]
+        for r in reqs:
+            assert srv._admit(r, 0.0)
+        while any(r.prefilled < len(r.prompt) for r in reqs):
+            owners, toks = srv.step_batch(reqs)
+            for r, t in zip(owners, toks):
+                r.out.append(int(t))
+        for _ in range(3):  # decode steps before the profiled one
+            owners, toks = srv.step_batch(reqs)
+            for r, t in zip(owners, toks):
+                r.out.append(int(t))
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("profiled")
+        srv.step_batch(reqs)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        assert sm.cm.device_status() == 0
+        sm.close()
+        print(json.dumps({"profile": args.profile, "batch": B, "ok": True}))
+        return
     if args.profile == "stack":
         model = synth.llama7b_layer(4)
     elif args.profile == "moe":
@@ -1106,7 +1136,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--serve", action="store_true", help="run the serving sweep instead")
-    ap.add_argument("--profile", choices=["stack", "fp8", "fp8prefill", "prefill", "decode", "moe"],
+    ap.add_argument("--profile", choices=["stack", "fp8", "fp8prefill", "prefill", "decode", "moe", "serve"],
                     help="small case for ncu")
     ap.add_argument("--rates", default="2,8,32")
     ap.add_argument("--bench-serve-rates", default="2,8,32",
