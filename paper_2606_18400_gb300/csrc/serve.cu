@@ -183,32 +183,59 @@ constexpr int NORM_VR = 8;  // d_model up to 8192 in registers
 
 // RoPE (rotate-half pairs (i, i+64) of a 128-dim head, angle pos * theta^(-i/64))
 // on q and k; k and v written to the paged cache [block][16][n_kv][128].
-__global__ void k_rope_cache(__nv_bfloat16 *q, const __nv_bfloat16 *k, const __nv_bfloat16 *v,
-                             const int32_t *pos, const int32_t *req, const int32_t *btab,
-                             int max_blocks, int HQ, int HKV, float theta, __nv_bfloat16 *kc,
-                             __nv_bfloat16 *vc) {
+// One block per token: the 64 angles of its position are computed once and
+// shared by all its heads; a thread rotates 8 pairs of one head (16-byte
+// loads and stores of each half).
+__device__ __forceinline__ void rope8(uint4 &lo, uint4 &hi, const float *cs, const float *sn) {
+    __nv_bfloat162 *l2 = reinterpret_cast<__nv_bfloat162 *>(&lo);
+    __nv_bfloat162 *h2 = reinterpret_cast<__nv_bfloat162 *>(&hi);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float2 a = __bfloat1622float2(l2[j]), b = __bfloat1622float2(h2[j]);
+        const float c0 = cs[2 * j], s0 = sn[2 * j], c1 = cs[2 * j + 1], s1 = sn[2 * j + 1];
+        l2[j] = __floats2bfloat162_rn(a.x * c0 - b.x * s0, a.y * c1 - b.y * s1);
+        h2[j] = __floats2bfloat162_rn(b.x * c0 + a.x * s0, b.y * c1 + a.y * s1);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_rope_cache(__nv_bfloat16 *q, const __nv_bfloat16 *k,
+                                                    const __nv_bfloat16 *v, const int32_t *pos,
+                                                    const int32_t *req, const int32_t *btab, int max_blocks,
+                                                    int HQ, int HKV, float theta, __nv_bfloat16 *kc,
+                                                    __nv_bfloat16 *vc) {
     chain_enter();
-    const int m = blockIdx.x, head = blockIdx.y, i = threadIdx.x;  // i < 64
+    __shared__ float cs_s[64], sn_s[64];
+    const int m = blockIdx.x;
     const int p = pos[m];
-    const float freq = powf(theta, -(float)i / 64.0f);
-    float sn, cs;
-    sincosf((float)p * freq, &sn, &cs);
-    if (head < HQ) {
-        __nv_bfloat16 *qh = q + ((size_t)m * HQ + head) * 128;
-        const float a = __bfloat162float(qh[i]), b = __bfloat162float(qh[i + 64]);
-        qh[i] = __float2bfloat16_rn(a * cs - b * sn);
-        qh[i + 64] = __float2bfloat16_rn(b * cs + a * sn);
-    } else {
-        const int kh = head - HQ;  // < HKV
-        const __nv_bfloat16 *kr = k + ((size_t)m * HKV + kh) * 128;
-        const __nv_bfloat16 *vr = v + ((size_t)m * HKV + kh) * 128;
-        const int blk = btab[(size_t)req[m] * max_blocks + p / 16];
-        const size_t off = (((size_t)blk * 16 + p % 16) * HKV + kh) * 128;
-        const float a = __bfloat162float(kr[i]), b = __bfloat162float(kr[i + 64]);
-        kc[off + i] = __float2bfloat16_rn(a * cs - b * sn);
-        kc[off + i + 64] = __float2bfloat16_rn(b * cs + a * sn);
-        vc[off + i] = vr[i];
-        vc[off + i + 64] = vr[i + 64];
+    if (threadIdx.x < 64) {
+        const int i = threadIdx.x;
+        const float freq = powf(theta, -(float)i / 64.0f);
+        sincosf((float)p * freq, &sn_s[i], &cs_s[i]);
+    }
+    __syncthreads();
+    const int blk = HKV > 0 ? btab[(size_t)req[m] * max_blocks + p / 16] : 0;
+    for (int w = threadIdx.x; w < (HQ + HKV) * 8; w += blockDim.x) {
+        const int head = w >> 3, i0 = (w & 7) * 8;  // pairs i0 .. i0 + 7
+        if (head < HQ) {
+            uint4 *qh = reinterpret_cast<uint4 *>(q + ((size_t)m * HQ + head) * 128);
+            uint4 lo = qh[i0 / 8], hi = qh[8 + i0 / 8];
+            rope8(lo, hi, cs_s + i0, sn_s + i0);
+            qh[i0 / 8] = lo;
+            qh[8 + i0 / 8] = hi;
+        } else {
+            const int kh = head - HQ;  // < HKV
+            const uint4 *kr = reinterpret_cast<const uint4 *>(k + ((size_t)m * HKV + kh) * 128);
+            const uint4 *vr = reinterpret_cast<const uint4 *>(v + ((size_t)m * HKV + kh) * 128);
+            const size_t off = (((size_t)blk * 16 + p % 16) * HKV + kh) * 128;
+            uint4 lo = kr[i0 / 8], hi = kr[8 + i0 / 8];
+            rope8(lo, hi, cs_s + i0, sn_s + i0);
+            uint4 *kd = reinterpret_cast<uint4 *>(kc + off);
+            uint4 *vd = reinterpret_cast<uint4 *>(vc + off);
+            kd[i0 / 8] = lo;
+            kd[8 + i0 / 8] = hi;
+            vd[i0 / 8] = vr[i0 / 8];
+            vd[8 + i0 / 8] = vr[8 + i0 / 8];
+        }
     }
 }
 
@@ -570,12 +597,24 @@ __global__ void k_add(float *h, const float *y, size_t n) {
     if (i < n) h[i] += y[i];
 }
 
+// act = bf16(silu(g) * u), four elements per thread (16-byte loads; the
+// buffers are 256-byte aligned), a scalar tail
 __global__ void k_silu_mul(const float *g, const float *u, __nv_bfloat16 *act, size_t n) {
     chain_enter();
-    const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    if (i < n) {
-        const float a = g[i];
-        act[i] = __float2bfloat16_rn(a / (1.0f + expf(-a)) * u[i]);
+    const size_t i = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) * 4;
+    if (i + 4 > n) {
+        for (size_t e = i; e < n; ++e) act[e] = __float2bfloat16_rn(g[e] / (1.0f + expf(-g[e])) * u[e]);
+        return;
+    }
+    {
+        const float4 a = *reinterpret_cast<const float4 *>(g + i);
+        const float4 b = *reinterpret_cast<const float4 *>(u + i);
+        const __nv_bfloat162 lo = __floats2bfloat162_rn(a.x / (1.0f + expf(-a.x)) * b.x,
+                                                        a.y / (1.0f + expf(-a.y)) * b.y);
+        const __nv_bfloat162 hi = __floats2bfloat162_rn(a.z / (1.0f + expf(-a.z)) * b.z,
+                                                        a.w / (1.0f + expf(-a.w)) * b.w);
+        *reinterpret_cast<uint2 *>(act + i) =
+            make_uint2(*reinterpret_cast<const uint32_t *>(&lo), *reinterpret_cast<const uint32_t *>(&hi));
     }
 }
 
@@ -746,7 +785,7 @@ static cloak_status serve_step_body(cloak_ctx *ctx, const cloak_serve_desc *d,
             void *ys3[3] = {q, k, v};
             if ((rc = step_linears(ctx, 3, ts, xs3, ys3, M, m_dec, CLOAK_OUT_BF16, flags, s))) return rc;
         }
-        CLOAK_CUDA(ctx, launch_k(ctx->chained, k_rope_cache, dim3(M, HQ + HKV), dim3(64), 0, s, q, k, v,
+        CLOAK_CUDA(ctx, launch_k(ctx->chained, k_rope_cache, dim3(M), dim3(256), 0, s, q, k, v,
                                  b->positions, b->req_slots, b->block_tables, d->max_blocks, HQ, HKV,
                                  d->rope_theta, kc, vc));
         CLOAK_LAUNCHED(ctx);
@@ -777,7 +816,7 @@ static cloak_status serve_step_body(cloak_ctx *ctx, const cloak_serve_desc *d,
             void *ys2[2] = {g, u};
             if ((rc = step_linears(ctx, 2, ts, xs2, ys2, M, m_dec, CLOAK_OUT_F32, flags, s))) return rc;
         }
-        CLOAK_CUDA(ctx, launch_k(ctx->chained, k_silu_mul, dim3(nb(Mz * F)), dim3(256), 0, s, g, u, act,
+        CLOAK_CUDA(ctx, launch_k(ctx->chained, k_silu_mul, dim3(nb((Mz * F + 3) / 4)), dim3(256), 0, s, g, u, act,
                                  Mz * F));
         CLOAK_LAUNCHED(ctx);
         {
