@@ -405,7 +405,9 @@ typedef struct {
      * of consecutive tokens of one request at consecutive positions, whose
      * queries share staged K/V tiles; single_rows[num_single]: the other
      * tokens, one block each. Together they must cover every token once. A
-     * token's result depends only on which of the two lists holds it. */
+     * token's result depends only on which of the two lists holds it; the
+     * qtiles order is the order their blocks start (latest positions first
+     * balances the work). */
     int32_t num_qtiles, num_single;
     const int32_t *qtiles, *single_rows;
 } cloak_serve_batch;

@@ -433,7 +433,9 @@ __global__ void __launch_bounds__(128) k_attention_tiled(const __nv_bfloat16 *q,
                                                          int HKV, __nv_bfloat16 *out) {
     chain_enter();
     extern __shared__ __align__(128) uint8_t att_smem[];  // [2 buffers][K tile, V tile]
-    const int tile = blockIdx.x, j = blockIdx.y, t = threadIdx.x;
+    // blocks start in list order, all heads of a tile together: a list with
+    // the latest positions (the most keys) first leaves the light tiles last
+    const int tile = blockIdx.y, j = blockIdx.x, t = threadIdx.x;
     const int warp = t >> 5, lane = t & 31;
     const int first = tiles[3 * tile], nq = tiles[3 * tile + 1];
     const int kvh = j / (HQ / HKV);
@@ -697,7 +699,8 @@ static cloak_status serve_step_body(cloak_ctx *ctx, const cloak_serve_desc *d,
     // single-query attention: every token without a work split, split over the keys
     const int n_single = b->qtiles ? b->num_single : M;
     const int32_t *single = b->qtiles ? b->single_rows : nullptr;
-    if (n_single < 0 || n_single > M || (b->qtiles && (b->num_qtiles < 0 || (n_single && !single))))
+    if (n_single < 0 || n_single > M ||
+        (b->qtiles && (b->num_qtiles < 0 || b->num_qtiles > 65535 || (n_single && !single))))
         return CLOAK_E_INVAL;
     const int max_splits = (d->max_blocks * 16 + ATT_SPLIT - 1) / ATT_SPLIT;
     const size_t part_bytes = (size_t)std::max(n_single, 1) * HQ * max_splits * ATT_PART * 4;
@@ -791,7 +794,7 @@ static cloak_status serve_step_body(cloak_ctx *ctx, const cloak_serve_desc *d,
         CLOAK_LAUNCHED(ctx);
         if (b->qtiles && b->num_qtiles > 0) {
             // prefill runs: query tiles sharing staged K/V tiles
-            CLOAK_CUDA(ctx, launch_k(ctx->chained, k_attention_tiled, dim3(b->num_qtiles, HQ), dim3(128),
+            CLOAK_CUDA(ctx, launch_k(ctx->chained, k_attention_tiled, dim3(HQ, b->num_qtiles), dim3(128),
                                      4 * ATT_TILE_BYTES, s, q, kc, vc, b->positions, b->req_slots,
                                      b->block_tables, b->qtiles, d->max_blocks, HQ, HKV, attn));
             CLOAK_LAUNCHED(ctx);

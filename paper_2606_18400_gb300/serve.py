@@ -227,6 +227,11 @@ class Server:
         M, S = len(ids), len(samp)
         if M == 0:
             return [], []
+        # query tiles with the most keys (latest last position) first: the
+        # attention kernel starts them first and the light ones fill the tail
+        tri = [tiles[i:i + 3] for i in range(0, len(tiles), 3)]
+        tri.sort(key=lambda t: -pos[t[0] + t[1] - 1])
+        tiles = [v for t in tri for v in t]
         self.h_ids[:M] = torch.tensor(ids, dtype=torch.int32)
         self.h_pos[:M] = torch.tensor(pos, dtype=torch.int32)
         self.h_req[:M] = torch.tensor(req, dtype=torch.int32)
