@@ -162,11 +162,12 @@ def test_linear_host_entry_point(cloak_lib):
     cm.close()
 
 
-@pytest.mark.parametrize("layout", ["packed", "separate", "pageable"])
+@pytest.mark.parametrize("layout", ["packed", "separate", "pageable", "unaligned"])
 def test_batch_host_entry_point(cloak_lib, layout):
     """The grouped launch from host buffers equals the same launch on device
     buffers bit for bit, whether the host vectors lie back to back (one copy
-    each way), apart, or in pageable memory."""
+    each way), apart, in pageable memory, or in pinned memory at 2-byte
+    offsets."""
     m = synth.small_decoder(1, synth.DT_BF16, d_model=384, n_heads=6, n_kv_heads=2, d_ff=200)
     cm, om, tb, arena, scales, Ws = place_both(cloak_lib, m, key=0x5A)
     M = 3
@@ -174,10 +175,11 @@ def test_batch_host_entry_point(cloak_lib, layout):
     xs = [torch.from_numpy(synth.activations_host(M, m.tensors[t].k, seed=70 + t)).to(torch.bfloat16)
           for t in ts]
     pin = layout != "pageable"
-    if layout == "packed":
-        xbuf = torch.cat([x.reshape(-1) for x in xs]).pin_memory()
-        ybuf = torch.empty(sum(M * m.tensors[t].n for t in ts), dtype=torch.float32).pin_memory()
-        xh, yh, o, q = [], [], 0, 0
+    if layout in ("packed", "unaligned"):
+        sh = 1 if layout == "unaligned" else 0
+        xbuf = torch.cat([torch.zeros(sh, dtype=torch.bfloat16)] + [x.reshape(-1) for x in xs]).pin_memory()
+        ybuf = torch.empty(sum(M * m.tensors[t].n for t in ts) + sh, dtype=torch.float32).pin_memory()
+        xh, yh, o, q = [], [], sh, sh
         for t, x in zip(ts, xs):
             xh.append(xbuf[o:o + x.numel()].view(M, -1))
             o += x.numel()
