@@ -930,6 +930,8 @@ def run_cloak(args):
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
                          "unit": "GB/s", "frac": round(achieved / hbm, 4),
                          "traffic": traffic, "peak_source": peak_note,
+                         "peak_kind": "copy bandwidth (read + write) measured on this GPU; the step is a "
+                                      "read stream (2.4 MB written per 405 MB read)",
                          "kernel": "k_linear_tc<bf16, N=16>: one launch, 7 linears, swap-AB tcgen05, stream-K",
                          "kernel_us": round(ms * 1e3, 2),
                          "kernel_us_source": "CUDA events around the timed region (one replay of a graph "
