@@ -176,7 +176,7 @@ static void release(cloak_ctx *c) {
     if (c->flags & CLOAK_MODEL_VMM) vmm_release(c); else F(c->arena);
     F(c->twin); F(c->d_scales); F(c->d_part); F(c->d_rowcnt); F(c->d_xq);
     F(c->d_xs); F(c->d_xstage); F(c->d_ystage); F(c->d_plan); F(c->d_status);
-    F(c->d_stack_ws); F(c->d_serve_ws); F(c->d_att_cnt); F(c->d_slot_old); F(c->d_tile_tmp); F(c->d_moe_ws); F(c->rk.d_owner); F(c->d_xqp); F(c->d_xsg); F(c->d_gemm_next);
+    F(c->d_stack_ws); F(c->d_serve_ws); F(c->d_att_cnt); F(c->d_slot_old); F(c->d_slot_inv); F(c->d_tile_tmp); F(c->d_moe_ws); F(c->rk.d_owner); F(c->d_xqp); F(c->d_xsg); F(c->d_gemm_next);
     for (auto &h : c->h_upload_stage)
         if (h) cudaFreeHost(h);
     if (c->rk.copied) cudaEventDestroy(c->rk.copied);

@@ -128,6 +128,7 @@ struct cloak_ctx {
     uint32_t *d_plan = nullptr;                // re-key move plan
     size_t plan_cap = 0;
     uint32_t *d_slot_old = nullptr;            // tile-level re-key: the gather table before it
+    uint32_t *d_slot_inv = nullptr;            // tile-level re-key: new slot -> tile (NONE: empty)
     uint8_t *d_tile_tmp = nullptr;             // tile-level re-key out of place: an arena-sized buffer,
                                                // allocated by the first such re-key and kept
     // concurrent re-key in progress (cloak_rekey_begin / cloak_rekey_advance)

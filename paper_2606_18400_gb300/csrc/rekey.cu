@@ -571,15 +571,26 @@ __global__ void k_zero_tail_slots(const uint32_t *page_alloc, uint32_t G, uint32
 // Out-of-place tile moves: tile g from its old slot in the arena to its new
 // slot in `tmp` (an arena-sized buffer); one tile per block iteration, each
 // thread's 16-byte loads of the tile all in flight before its stores.
+// new slot -> tile (the inverse of the new gather table; inv starts all NONE)
+__global__ void k_slot_inverse(const uint32_t *__restrict__ new_slot, uint32_t G, uint32_t *__restrict__ inv) {
+    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < G) inv[new_slot[g]] = g;
+}
+
+// Every tile from its old slot in the arena to its new slot in tmp, taken in
+// new-slot order: the blocks running at one time write one run of tmp (the
+// reads are scattered either way).
 __global__ void __launch_bounds__(256) k_tile_gather(const uint32_t *__restrict__ old_slot,
-                                                     const uint32_t *__restrict__ new_slot, uint32_t G,
+                                                     const uint32_t *__restrict__ inv, uint32_t nslots,
                                                      const uint8_t *__restrict__ arena, uint8_t *__restrict__ tmp,
                                                      int64_t tile_bytes) {
     constexpr int PT = 8;  // 16-byte pieces per thread and round: 32 KiB per block round
     const int64_t n16 = tile_bytes / 16;
-    for (uint32_t g = blockIdx.x; g < G; g += gridDim.x) {
+    for (uint32_t d = blockIdx.x; d < nslots; d += gridDim.x) {
+        const uint32_t g = inv[d];
+        if (g == NONE) continue;
         const uint4 *src = reinterpret_cast<const uint4 *>(arena + (int64_t)old_slot[g] * tile_bytes);
-        uint4 *dst = reinterpret_cast<uint4 *>(tmp + (int64_t)new_slot[g] * tile_bytes);
+        uint4 *dst = reinterpret_cast<uint4 *>(tmp + (int64_t)d * tile_bytes);
         for (int64_t i0 = 0; i0 < n16; i0 += (int64_t)PT * blockDim.x) {
             uint4 v[PT];
 #pragma unroll
@@ -627,8 +638,14 @@ cloak_status tile_rekey_run(cloak_ctx *ctx, uint64_t key, uint32_t new_epoch, cu
         cudaGetLastError();  // the failed allocation is not a sticky error
     }
     if (!in_place && ctx->d_tile_tmp) {
-        k_tile_gather<<<ctx->sm_count * 8, 256, 0, s>>>(ctx->d_slot_old, ctx->d_tile_slot, (uint32_t)ctx->G,
-                                                        ctx->arena, ctx->d_tile_tmp, ctx->tile_bytes);
+        const uint32_t nslots = (uint32_t)(ctx->NPS * ctx->tpp);
+        if (!ctx->d_slot_inv) CLOAK_CUDA(ctx, cudaMalloc(&ctx->d_slot_inv, (size_t)nslots * 4));
+        CLOAK_CUDA(ctx, cudaMemsetAsync(ctx->d_slot_inv, 0xFF, (size_t)nslots * 4, s));
+        k_slot_inverse<<<(unsigned)((ctx->G + 255) / 256), 256, 0, s>>>(ctx->d_tile_slot, (uint32_t)ctx->G,
+                                                                         ctx->d_slot_inv);
+        CLOAK_LAUNCHED(ctx);
+        k_tile_gather<<<ctx->sm_count * 8, 256, 0, s>>>(ctx->d_slot_old, ctx->d_slot_inv, nslots, ctx->arena,
+                                                        ctx->d_tile_tmp, ctx->tile_bytes);
         ctx->launches++;
         cudaError_t e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->arena, ctx->d_tile_tmp, bytes, cudaMemcpyDeviceToDevice, s);
