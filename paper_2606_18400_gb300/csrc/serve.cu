@@ -240,8 +240,8 @@ __global__ void __launch_bounds__(256) k_rope_cache(__nv_bfloat16 *q, const __nv
 }
 
 // Causal attention of single queries (decode tokens), split over the keys:
-// block (split, row, head) takes keys [64 split, 64 split + 64) of token
-// m = rows[row]; each of its 4 warps 16 of them, 8 at a time. A lane holds 4
+// block (split, row, head) takes keys [128 split, 128 split + 128) of token
+// m = rows[row]; each of its 4 warps 32 of them, 8 at a time. A lane holds 4
 // of the 128 dimensions: K and V rows are read as 256-byte coalesced warp
 // loads, 16 of them in flight per lane; scores are warp sums. Online softmax
 // in FP32 per warp, merged across the warps in shared memory. A token with
@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(256) k_rope_cache(__nv_bfloat16 *q, const __nv
 // acc[128]) and the last of the token's blocks to finish (an arrival count
 // per token and head) merges the splits in order. The split depends only on
 // the token's own position, so the result does not depend on the batch.
-constexpr int ATT_SPLIT = 64;
+constexpr int ATT_SPLIT = 128;
 constexpr int ATT_PART = 132;  // floats per partial: max, sum, pad, acc[128]
 constexpr int ATT_GRID_X = 16;  // blocks per (token, head); longer contexts loop
 

@@ -88,14 +88,14 @@ def test_serve_step_matches_full_model_oracle(served, tiled, decode_first):
 
 
 def test_decode_attention_over_a_long_context(cloak_lib):
-    """A prompt of 1,100 tokens: each decode token attends over 18 key
-    splits, more than the blocks of one (token, head), so blocks take several
-    splits and the last to finish merges them. Logits against the FP64 model;
-    the request alone equals the request next to a short one."""
+    """A prompt of 2,200 tokens: each decode token attends over 18 key
+    splits of 128, more than the blocks of one (token, head), so blocks take
+    several splits and the last to finish merges them. Logits against the
+    FP64 model; the request alone equals the request next to a short one."""
     m = small_served()
     Ws = synth.weights_host(m, seed=0, std=0.05)
-    sm = serve.ServedModel(m, kv_blocks=256, max_blocks=80, twin=True, weights=Ws)
-    long = list(np.random.default_rng(11).integers(0, 1000, 1100))
+    sm = serve.ServedModel(m, kv_blocks=400, max_blocks=160, twin=True, weights=Ws)
+    long = list(np.random.default_rng(11).integers(0, 1000, 2200))
     short = list(np.random.default_rng(12).integers(0, 1000, 40))
     la, sa = run_steps(sm, [(0, long)], tiled=True)
     lm, _ = run_steps(sm, [(1, short), (0, long)], tiled=True)
@@ -106,7 +106,7 @@ def test_decode_attention_over_a_long_context(cloak_lib):
     seq = sa[0]
     ref = O.transformer_logits_f64(m, W64, emb64, seq[:-1])
     for step, lg in enumerate(la[0]):
-        p = 1099 + step
+        p = 2199 + step
         assert O.relative_error(lg, ref[p]) <= 1e-2, (step, O.relative_error(lg, ref[p]))
     sm.close()
 
