@@ -27,10 +27,11 @@ def served(cloak_lib):
     sm.close()
 
 
-def run_steps(sm, seqs, uncloaked=False, tiled=False, decode_first=False):
+def run_steps(sm, seqs, uncloaked=False, tiled=False, decode_first=False, tile=64):
     """Prefill each (slot, tokens) fully in one step, then decode 3 steps
     feeding back greedy tokens; returns per slot the list of logits. With
-    `tiled`, prefill tokens use query tiles (64) and decode tokens single rows."""
+    `tiled`, prefill tokens use query tiles (`tile` tokens, at most 64) and
+    decode tokens single rows."""
     dev = "cuda"
     bt = torch.zeros((8, sm.max_blocks), dtype=torch.int32, device=dev)
     for slot, toks in seqs:
@@ -43,8 +44,8 @@ def run_steps(sm, seqs, uncloaked=False, tiled=False, decode_first=False):
         for slot, toks in seqs:
             seq = state[slot]
             if first:
-                for t0 in range(0, len(seq), 64):
-                    tiles += [len(ids) + t0, min(64, len(seq) - t0), 0]
+                for t0 in range(0, len(seq), tile):
+                    tiles += [len(ids) + t0, min(tile, len(seq) - t0), 0]
                 for i, t in enumerate(seq):
                     ids.append(t); pos.append(i); req.append(slot)
             else:
@@ -68,23 +69,26 @@ def run_steps(sm, seqs, uncloaked=False, tiled=False, decode_first=False):
     return logits, state
 
 
-@pytest.mark.parametrize("tiled,decode_first", [(False, False), (True, False), (True, True)])
-def test_serve_step_matches_full_model_oracle(served, tiled, decode_first):
+@pytest.mark.parametrize("tiled,decode_first,tile", [(False, False, 64), (True, False, 64), (True, True, 64),
+                                                    (True, True, 48)])
+def test_serve_step_matches_full_model_oracle(served, tiled, decode_first, tile):
     """decode_first: the prompt rows take the prefill GEMM, decode rows the
-    split-K kernel."""
+    split-K kernel. Query tiles of 64 or 48 tokens (not aligned to the
+    64-key tiles)."""
     m, Ws, sm = served
-    toks = list(np.random.default_rng(1).integers(0, 1000, 23))
-    logits, state = run_steps(sm, [(0, toks)], tiled=tiled, decode_first=decode_first)
+    toks = list(np.random.default_rng(1).integers(0, 1000, 23 if tile == 64 else 200))
+    logits, state = run_steps(sm, [(0, toks)], tiled=tiled, decode_first=decode_first, tile=tile)
     W64 = [O.bf16_value(O.bf16_bits(w)) for w in Ws]
     emb64 = O.bf16_value(O.bf16_bits(synth.embedding_host(1000, 512)))
     seq = state[0]
     ref = O.transformer_logits_f64(m, W64, emb64, seq[:-1])
+    L = len(toks)
     for step, lg in enumerate(logits[0]):
-        p = 22 + step  # position whose next token was sampled
+        p = L - 1 + step  # position whose next token was sampled
         assert O.relative_error(lg, ref[p]) <= 1e-2, (step, O.relative_error(lg, ref[p]))
         top = np.sort(ref[p])[-2:]
         if top[1] - top[0] > 0.05 * np.std(ref[p]):
-            assert seq[23 + step] == int(np.argmax(ref[p]))
+            assert seq[L + step] == int(np.argmax(ref[p]))
 
 
 def test_decode_attention_over_a_long_context(cloak_lib):
