@@ -1043,6 +1043,8 @@ def run_profile(args):
     serve  -- the 32-layer served model (13.4 GB) with --M requests of 1,000-token
               prompts prefilled, then one decode-only step (all kernels of the step;
               for launch lists: the KV cache makes it up to 35 GB at --M 64).
+    serveprefill -- the same model, one step that prefills a prompt of --M tokens
+              (one request; prefill GEMM, query-tiled attention).
     The linears' launch shape is tuned first (unless --no-tune); the profiled
     launches sit inside the NVTX range "profiled" (ncu --nvtx
     --nvtx-include "profiled/")."""
@@ -1050,6 +1052,28 @@ def run_profile(args):
     from paper_2606_18400_gb300 import cloak, synth
     cloak.load()
     torch.cuda.set_device(0)
+    if args.profile == "serveprefill":
+        from paper_2606_18400_gb300 import serve
+        P = args.M
+        sm = serve.ServedModel(synth.serving_model(32, 32000), kv_blocks=(P + 15) // 16 * 2 + 8,
+                               max_blocks=(P + 15) // 16 + 2, twin=False)
+        srv = serve.Server(sm, max_running=64, token_budget=max(2048, P), rekey_period=None)
+        rng = np.random.default_rng(P)
+        for rep in range(2):  # the first step warms up; the second is profiled
+            r = serve.Request(rep, 0.0, rng.integers(0, 32000, P).astype(np.int32), 4)
+            assert srv._admit(r, 0.0)
+            torch.cuda.synchronize()
+            if rep:
+                torch.cuda.nvtx.range_push("profiled")
+            srv.step_batch([r])
+            torch.cuda.synchronize()
+            if rep:
+                torch.cuda.nvtx.range_pop()
+            srv._release(r)
+        assert sm.cm.device_status() == 0
+        sm.close()
+        print(json.dumps({"profile": args.profile, "prompt": P, "ok": True}))
+        return
     if args.profile == "serve":
         from paper_2606_18400_gb300 import serve
         B = args.M
@@ -1138,7 +1162,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--serve", action="store_true", help="run the serving sweep instead")
-    ap.add_argument("--profile", choices=["stack", "fp8", "fp8prefill", "prefill", "decode", "moe", "serve"],
+    ap.add_argument("--profile", choices=["stack", "fp8", "fp8prefill", "prefill", "decode", "moe", "serve", "serveprefill"],
                     help="small case for ncu")
     ap.add_argument("--rates", default="2,8,32")
     ap.add_argument("--bench-serve-rates", default="2,8,32",
