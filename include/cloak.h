@@ -418,7 +418,11 @@ typedef struct {
  * gate/up, SiLU-gated product, cloaked down + residual; then RMSNorm, the
  * cloaked lm_head at the sampled rows and greedy argmax. Enqueued on `stream`;
  * the context-owned workspace grows with the batch. A token's results depend
- * only on its own request, so a request computes the same alone or batched. */
+ * only on its own request, so a request computes the same alone or batched.
+ * The step's first kernel is an ordinary launch (it follows whatever the
+ * caller enqueued, e.g. a concurrent re-key's table update); the later ones
+ * are programmatic dependent launches of one another, each waiting for its
+ * predecessor before it reads that kernel's outputs. */
 CLOAK_API cloak_status cloak_serve_step(cloak_ctx *ctx, const cloak_serve_desc *desc,
                                         const cloak_serve_batch *batch, void *stream);
 
