@@ -241,7 +241,8 @@ __global__ void __launch_bounds__(256) k_rope_cache(__nv_bfloat16 *q, const __nv
 
 // Causal attention of single queries (decode tokens), split over the keys:
 // block (split, row, head) takes keys [128 split, 128 split + 128) of token
-// m = rows[row]; each of its 4 warps 32 of them, 8 at a time. A lane holds 4
+// m = rows[row]; each of its 4 warps 32 of them, 8 at a time (8 keys lie in
+// one 16-key block of the cache: one table entry per batch). A lane holds 4
 // of the 128 dimensions: K and V rows are read as 256-byte coalesced warp
 // loads, 16 of them in flight per lane; scores are warp sums. Online softmax
 // in FP32 per warp, merged across the warps in shared memory. A token with
@@ -286,12 +287,15 @@ __global__ void __launch_bounds__(128) k_attn_decode(const __nv_bfloat16 *q, con
         const int k_begin = sp * ATT_SPLIT + w * (ATT_SPLIT / 4);
         const int k_end = min(n, k_begin + ATT_SPLIT / 4);
         float mx = -FLT_MAX, sum = 0.0f, acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        const bool hi = (lane >> 4) & 1;
+        const size_t kstr = (size_t)HKV * 128;  // elements between consecutive keys of a cache block
         for (int kb = k_begin; kb < k_end; kb += 8) {
+            // kb is a multiple of 8: the 8 keys lie in one 16-key block of the cache
+            const size_t base = (((size_t)bt[kb >> 4] * 16 + (kb & 15)) * HKV + kvh) * 128 + 4 * lane;
             uint2 kr[8], vr[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
-                const int key = min(kb + i, k_end - 1);
-                const size_t off = (((size_t)bt[key >> 4] * 16 + (key & 15)) * HKV + kvh) * 128 + 4 * lane;
+                const size_t off = base + (size_t)(min(kb + i, k_end - 1) - kb) * kstr;
                 kr[i] = *reinterpret_cast<const uint2 *>(kc + off);
                 vr[i] = *reinterpret_cast<const uint2 *>(vc + off);
             }
@@ -302,10 +306,27 @@ __global__ void __launch_bounds__(128) k_attn_decode(const __nv_bfloat16 *q, con
                 const float2 a = __bfloat1622float2(h2[0]), b = __bfloat1622float2(h2[1]);
                 s[i] = fmaf(qd[0], a.x, fmaf(qd[1], a.y, fmaf(qd[2], b.x, qd[3] * b.y)));
             }
+            // sums over the 32 lanes: lane bit 4 splits the keys 4/4 (each half
+            // keeps its four and adds the partner's copy of them), bits 3..0
+            // finish the sums, and one exchange gives every lane all eight
+            {
+                float t4[4];
 #pragma unroll
-            for (int o = 16; o; o >>= 1) {
+                for (int i = 0; i < 4; ++i) {
+                    const float mine = hi ? s[i + 4] : s[i], give = hi ? s[i] : s[i + 4];
+                    t4[i] = mine + __shfl_xor_sync(0xffffffffu, give, 16);
+                }
 #pragma unroll
-                for (int i = 0; i < 8; ++i) s[i] += __shfl_xor_sync(0xffffffffu, s[i], o);
+                for (int o = 8; o; o >>= 1) {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) t4[i] += __shfl_xor_sync(0xffffffffu, t4[i], o);
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float other = __shfl_xor_sync(0xffffffffu, t4[i], 16);
+                    s[i] = hi ? other : t4[i];
+                    s[i + 4] = hi ? t4[i] : other;
+                }
             }
             float cm = mx;
 #pragma unroll
