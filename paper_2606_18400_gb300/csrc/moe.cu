@@ -156,8 +156,11 @@ struct GemvArgs {
     int rows;                 // valid rows (d_ff or d_model)
 };
 
-template <int EP>
-__global__ void __launch_bounds__(256) k_moe_gemv(GemvArgs a) {
+// MINB: CTAs per SM the registers allow (2: about 100 registers; 3: 80, a few
+// spilled, the variant for batches of more than one token, whose experts
+// fill one wave of three CTAs per SM where two would need two waves)
+template <int EP, int MINB = 2>
+__global__ void __launch_bounds__(256, MINB) k_moe_gemv(GemvArgs a) {
     int b = blockIdx.x;
     const int kc = b % a.kc_n; b /= a.kc_n;
     const int nt = b % a.nt_n; b /= a.nt_n;
@@ -270,16 +273,16 @@ __global__ void __launch_bounds__(256) k_moe_gemv(GemvArgs a) {
 }
 
 // K chunks (at most `cap`: the epilogues' unrolled sums): the count whose
-// waves of two CTAs per SM (the GEMV's register use) take the least time,
-// a block costing its tiles plus about three tiles' worth of fixed latency
-// (table lookup, first load, arrival); fewer chunks on a tie
-int chunks_for(int blocks_per_chunk, int kt_n, int sms, int cap) {
+// waves of `per_sm` CTAs per SM take the least time, a block costing its
+// tiles plus about three tiles' worth of fixed latency (table lookup, first
+// load, arrival); fewer chunks on a tie
+int chunks_for(int blocks_per_chunk, int kt_n, int sms, int cap, int per_sm) {
     int best = 1;
     long best_t = -1;
     for (int kc = 1; kc <= std::min(kt_n, cap); ++kc) {
         const int ks = (kt_n + kc - 1) / kc;
         if ((kt_n + ks - 1) / ks != kc) continue;  // the same split as a smaller count
-        const long waves = ((long)blocks_per_chunk * kc + 2 * sms - 1) / (2 * sms);
+        const long waves = ((long)blocks_per_chunk * kc + per_sm * sms - 1) / ((long)per_sm * sms);
         const long t = waves * (ks + 3);
         if (best_t < 0 || t < best_t) {
             best_t = t;
@@ -328,8 +331,11 @@ cloak_status moe_run(cloak_ctx *ctx, const cloak_moe_desc *d, const void *x, flo
     // epilogues' unrolled sums
     auto fit16 = [](int kc, int kt_n) { return std::max(kc, (kt_n + 15) / 16); };
     const int rkc = std::min(DT, 16);
-    const int kc1 = fit16(chunks_for(pairs * 2 * FT, DT, ctx->sm_count, 16), DT);
-    const int kc2 = fit16(chunks_for(pairs * DT, FT, ctx->sm_count, 4), FT);
+    // one token: two CTAs per SM; more: three (measured: M = 1 37.4 vs 39.4 us,
+    // M = 4 76 vs 81.7 us)
+    const int per_sm = M == 1 ? 2 : 3;
+    const int kc1 = fit16(chunks_for(pairs * 2 * FT, DT, ctx->sm_count, 16, per_sm), DT);
+    const int kc2 = fit16(chunks_for(pairs * DT, FT, ctx->sm_count, 4, per_sm), FT);
     if (rkc < (DT + 15) / 16 || kc1 > 16 || kc2 > 4) return CLOAK_E_UNSUPPORTED;  // d_model > 32768 or d_ff > 8192
     auto r256 = [](size_t n) { return (n + 255) & ~(size_t)255; };
     const size_t b_tab = r256((size_t)E * 3 * 4), b_cnt = r256((size_t)64 * (FT * MOE_MAX_K + DT) * 4),
@@ -399,7 +405,8 @@ cloak_status moe_run(cloak_ctx *ctx, const cloak_moe_desc *d, const void *x, flo
     g.cnt = cnt;
     g.act = act;
     g.rows = F;
-    CLOAK_CUDA(ctx, launch_k(true, k_moe_gemv<EP_GATE_UP>, dim3(pairs * 2 * FT * kc1), dim3(256), 0, s, g));
+    CLOAK_CUDA(ctx, launch_k(true, per_sm == 2 ? k_moe_gemv<EP_GATE_UP, 2> : k_moe_gemv<EP_GATE_UP, 3>,
+                             dim3(pairs * 2 * FT * kc1), dim3(256), 0, s, g));
     CLOAK_LAUNCHED(ctx);
     // 5-6. down; the last block of a token's tile row writes y
     g.x = act;
@@ -416,7 +423,8 @@ cloak_status moe_run(cloak_ctx *ctx, const cloak_moe_desc *d, const void *x, flo
     g.w = w;
     g.y = y;
     g.rows = D;
-    CLOAK_CUDA(ctx, launch_k(true, k_moe_gemv<EP_DOWN>, dim3(pairs * DT * kc2), dim3(256), 0, s, g));
+    CLOAK_CUDA(ctx, launch_k(true, per_sm == 2 ? k_moe_gemv<EP_DOWN, 2> : k_moe_gemv<EP_DOWN, 3>,
+                             dim3(pairs * DT * kc2), dim3(256), 0, s, g));
     CLOAK_LAUNCHED(ctx);
     return CLOAK_OK;
 }
